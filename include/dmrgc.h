@@ -1,0 +1,162 @@
+/*
+ * dmrgc -- circuit-DMRG compression sweep on one GB300 (sm_103a).
+ *
+ * C ABI of the library.  All compute runs in the library's own CUDA kernels on
+ * the stream given in dmrgc_options::cuda_stream (0 = the legacy default
+ * stream).  The library owns all device memory it allocates; callers own every
+ * host buffer they pass.  Inputs are copied before a call returns; outputs
+ * are written once the stream has been synchronised inside the call.  No
+ * exception crosses this boundary and the library never aborts or traps: every
+ * entry point returns a dmrgc_status and, on failure, leaves a message for
+ * dmrgc_last_error().
+ *
+ * Method (arXiv:2207.05612, Ayral, Louvet, Zhou, Lambert, Stoudenmire,
+ * Waintal): open-mode simulation (Sec. IV.C) in which every compression step
+ * (Sec. IV.B) applies K gate cycles to a matrix product state and finds the
+ * normalised MPS of bond dimension <= chi with the largest overlap with the
+ * result, sweeping over the MPS and optimising two neighbouring tensors at a
+ * time (the two-site variant named in Sec. IV.B; Eq. (scalarproduct) and
+ * Eq. (optimization) with the bond constraint imposed by a truncated SVD).
+ *
+ * Conventions:
+ *  - Qubit q sits at grid position (r, c) with q = r*cols + c.  MPS sites are
+ *    ordered as a snake down the columns (down column 0, up column 1, ...).
+ *  - A gate's matrix is row-major complex128 with re/im interleaved:
+ *    <s_q0 s_q1|U|t_q0 t_q1>, q0 the most significant bit (4x4, 32 doubles);
+ *    a one-qubit gate (q1 = -1) uses the first 8 doubles as a 2x2 matrix.
+ *  - Calls are stateful and ordered: create -> (apply_layer -> sweep)* ->
+ *    fidelity / amplitude / sample.  Out-of-order calls return DMRGC_ESTATE.
+ */
+#ifndef DMRGC_H
+#define DMRGC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrgc_ctx dmrgc_ctx;
+
+typedef enum {
+  DMRGC_OK = 0,
+  DMRGC_EINVAL = 1,    /* bad argument (null pointer, size out of range) */
+  DMRGC_ENOMEM = 2,    /* device or host allocation failed */
+  DMRGC_ECUDA = 3,     /* a CUDA runtime call failed */
+  DMRGC_ENOCONV = 4,   /* Jacobi SVD did not converge within max_jacobi_sweeps */
+  DMRGC_ENUMERIC = 5,  /* NaN/Inf or a zero overlap met during a sweep */
+  DMRGC_ETIMEOUT = 6,  /* a bounded device-side wait ran out */
+  DMRGC_ESTATE = 7     /* call made out of order */
+} dmrgc_status;
+
+/* Arithmetic of the contractions and of the SVD. */
+enum {
+  DMRGC_FP64 = 0,    /* complex128 storage, FP64 arithmetic on CUDA cores */
+  DMRGC_BF16X3 = 1,  /* complex64 storage, BF16 hi/lo split products (3 terms), FP32 accumulate */
+  DMRGC_TF32X3 = 2,  /* complex64 storage, TF32 hi/lo split products (3 terms), FP32 accumulate */
+  DMRGC_FP32 = 3     /* complex64 storage, FP32 arithmetic on CUDA cores */
+};
+
+typedef struct {
+  int rows, cols; /* grid shape; n_qubits must equal rows*cols */
+  int order;      /* 0 = snake along columns (the only order) */
+} dmrgc_grid;
+
+typedef struct {
+  int precision;              /* DMRGC_FP64 ... DMRGC_FP32 */
+  int svd_mode;               /* 0 = one-sided Jacobi (only mode) */
+  double sweep_rel_cutoff;    /* keep s_mu > cutoff * s_1 in the sweep SVD; <= 0: default
+                                 (1e-12 for FP64, 1e-6 otherwise) */
+  double zip_rel_cutoff;      /* same for the truncating steps of the zip-up guess; <= 0:
+                                 default (1e-5 for FP64, 1e-3 otherwise) */
+  int max_jacobi_sweeps;      /* <= 0: default 40 */
+  unsigned long long seed;    /* reserved */
+  void* cuda_stream;          /* cudaStream_t to launch on; NULL = default stream */
+  int timing;                 /* 1: record CUDA-event time per kernel class (dmrgc_stats) */
+} dmrgc_options;
+
+typedef struct {
+  int q0, q1;        /* qubit indices; q1 = -1 for a one-qubit gate */
+  double mat[32];    /* row-major complex128, re/im interleaved */
+} dmrgc_gate;
+
+/* Per-kernel-class accounting (only filled when options.timing = 1).
+ * Times are CUDA-event milliseconds on the library's stream, flops are the
+ * algorithmic real flops of the complex contractions (8 per complex MAC). */
+typedef struct {
+  double gemm_ms, gemm_flops;   /* all contractions (environments, X/Y, theta, Gram, gauge) */
+  long long gemm_launches;
+  double svd_ms;                /* Jacobi SVD incl. sort/gather */
+  long long svd_launches;
+  double mpo_ms;                /* layer MPO build */
+  double other_ms;              /* permutes, copies, norms */
+  long long updates;            /* two-site updates done */
+  long long kernel_launches;    /* every kernel the library launched */
+} dmrgc_stats;
+
+/* Fill *opt with defaults (FP64, Jacobi, default cutoffs, default stream). */
+dmrgc_status dmrgc_default_options(dmrgc_options* opt);
+
+/* Create a context for n_qubits = grid->rows * grid->cols qubits in |0...0>
+ * (the unentangled product state is an MPS with chi = 1, Sec. IV.A).
+ * chi: maximum bond dimension (1 .. 4096).  *out receives the context. */
+dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi,
+                          const dmrgc_options* opt, dmrgc_ctx** out);
+
+/* Start one compression step (Sec. IV.B) for the gates of one layer (K
+ * cycles, gates in time order).  Builds the layer MPO W_i[D,2,2,D] from the
+ * gates (one-qubit gates merged into the neighbouring two-qubit gates'
+ * site tensors, Sec. IV.B.2), then the initial guess by a zip-up of W.|Psi_Q>
+ * from both ends towards the centre site.  The partial fidelity f_delta of
+ * the previous step is committed to log F_tilde (Eq. Ftilde-sup).
+ * gates: host array of n_gates records, copied before return. */
+dmrgc_status dmrgc_apply_layer(dmrgc_ctx* ctx, const dmrgc_gate* gates, int n_gates);
+
+/* Run n_sweeps * (N-1) two-site updates of the current step on the bouncing
+ * schedule that starts at bond (m-1, m), m = N/2, moving left; n_sweeps = 2
+ * ends at bond (m, m+1) with the orthogonality centre on site m.
+ * Each update forms theta (Eq. scalarproduct), takes its truncated SVD and
+ * sets the block to the constrained optimum (Eq. optimization).
+ * f_last (may be NULL): partial fidelity f after the last update. */
+dmrgc_status dmrgc_sweep(dmrgc_ctx* ctx, int n_sweeps, double* f_last);
+
+/* log F_tilde = sum over steps of log f_delta (Eq. Ftilde-sup), including the
+ * current step's latest f; f_delta_last: that latest f (Eq. fa-sup).
+ * Either pointer may be NULL. */
+dmrgc_status dmrgc_fidelity(dmrgc_ctx* ctx, double* log_F_tilde, double* f_delta_last);
+
+/* Amplitudes <x|Psi> of count bitstrings (Sec. IV.A, the MPS definition).
+ * bits: host uint8 [count][n_qubits] in qubit order (0 or 1).
+ * out_re_im: host double [count][2]. */
+dmrgc_status dmrgc_amplitude(dmrgc_ctx* ctx, const unsigned char* bits, long long count,
+                             double* out_re_im);
+
+/* Draw count bitstrings from |<x|Psi>|^2 by sequential conditional sampling.
+ * Bit i (MPS site order) of sample j is 0 iff u < p(0 | earlier bits), with
+ * u the (j*N + i + 1)-th output of SplitMix64 seeded with `seed`, mapped to
+ * [0,1) with its top 53 bits.  out_bits: host uint8 [count][n_qubits], qubit order. */
+dmrgc_status dmrgc_sample(dmrgc_ctx* ctx, long long count, unsigned long long seed,
+                          unsigned char* out_bits);
+
+/* Current bond dimensions of the MPS (n_qubits-1 entries) and of the layer
+ * MPO (n_qubits-1 entries); either pointer may be NULL. */
+dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* ctx, int* mps_bonds, int* mpo_bonds);
+
+/* Copy the MPS tensors to the host as complex128: site i has shape
+ * [chi_{i-1}][2][chi_i] (row-major), concatenated; *centre receives the
+ * orthogonality-centre site.  out must hold dmrgc_mps_size() complex values. */
+long long dmrgc_mps_size(const dmrgc_ctx* ctx);
+dmrgc_status dmrgc_get_mps(const dmrgc_ctx* ctx, double* out_re_im, int* centre);
+
+/* Per-update partial fidelities of the current step (Sec. IV.B.1: they never
+ * decrease).  Writes min(cap, count) values; *count receives the number done. */
+dmrgc_status dmrgc_step_history(const dmrgc_ctx* ctx, double* f, int cap, int* count);
+
+dmrgc_status dmrgc_get_stats(const dmrgc_ctx* ctx, dmrgc_stats* out);
+dmrgc_status dmrgc_reset_stats(dmrgc_ctx* ctx);
+
+const char* dmrgc_last_error(const dmrgc_ctx* ctx);
+void dmrgc_destroy(dmrgc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRGC_H */

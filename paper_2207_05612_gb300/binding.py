@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libdmrgc (include/dmrgc.h): argument marshalling only.
+
+Every function here converts Python / numpy arguments to the C types and calls
+the C entry point of the same name; all compute runs in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libdmrgc.so")
+
+DMRGC_FP64, DMRGC_BF16X3, DMRGC_TF32X3, DMRGC_FP32 = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENUMERIC",
+          6: "ETIMEOUT", 7: "ESTATE"}
+
+
+class DmrgcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dmrgc {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("order", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("svd_mode", C.c_int),
+                ("sweep_rel_cutoff", C.c_double), ("zip_rel_cutoff", C.c_double),
+                ("max_jacobi_sweeps", C.c_int), ("seed", C.c_ulonglong),
+                ("cuda_stream", C.c_void_p), ("timing", C.c_int)]
+
+
+class Gate(C.Structure):
+    _fields_ = [("q0", C.c_int), ("q1", C.c_int), ("mat", C.c_double * 32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("gemm_ms", C.c_double), ("gemm_flops", C.c_double), ("gemm_launches", C.c_longlong),
+                ("svd_ms", C.c_double), ("svd_launches", C.c_longlong), ("mpo_ms", C.c_double),
+                ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdmrgc.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libdmrgc.so not built at {_LIB_PATH}; run "
+                              "`python -m paper_2207_05612_gb300.build`")
+        L = C.CDLL(_LIB_PATH)
+        P = C.POINTER
+        L.dmrgc_default_options.argtypes = [P(Options)]
+        L.dmrgc_create.argtypes = [C.c_int, P(Grid), C.c_int, P(Options), P(C.c_void_p)]
+        L.dmrgc_apply_layer.argtypes = [C.c_void_p, P(Gate), C.c_int]
+        L.dmrgc_sweep.argtypes = [C.c_void_p, C.c_int, P(C.c_double)]
+        L.dmrgc_fidelity.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
+        L.dmrgc_amplitude.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
+        L.dmrgc_sample.argtypes = [C.c_void_p, C.c_longlong, C.c_ulonglong, C.c_void_p]
+        L.dmrgc_bond_dims.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.dmrgc_mps_size.argtypes = [C.c_void_p]
+        L.dmrgc_mps_size.restype = C.c_longlong
+        L.dmrgc_get_mps.argtypes = [C.c_void_p, C.c_void_p, P(C.c_int)]
+        L.dmrgc_step_history.argtypes = [C.c_void_p, C.c_void_p, C.c_int, P(C.c_int)]
+        L.dmrgc_get_stats.argtypes = [C.c_void_p, P(Stats)]
+        L.dmrgc_reset_stats.argtypes = [C.c_void_p]
+        L.dmrgc_last_error.argtypes = [C.c_void_p]
+        L.dmrgc_last_error.restype = C.c_char_p
+        L.dmrgc_destroy.argtypes = [C.c_void_p]
+        L.dmrgc_destroy.restype = None
+        for name in ("dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+                     "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
+                     "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = lib().dmrgc_last_error(ctx).decode() if ctx else ""
+        raise DmrgcError(status, msg)
+
+
+def pack_gates(layer) -> "C.Array":
+    """[(q0, q1, U)] -> array of dmrgc_gate (row-major complex128, re/im interleaved)."""
+    arr = (Gate * max(len(layer), 1))()
+    for i, (q0, q1, u) in enumerate(layer):
+        flat = np.asarray(u, dtype=np.complex128).reshape(-1)
+        buf = np.zeros(32)
+        buf[0:2 * flat.size:2] = flat.real
+        buf[1:2 * flat.size:2] = flat.imag
+        arr[i].q0 = int(q0)
+        arr[i].q1 = int(q1)
+        arr[i].mat[:] = buf.tolist()
+    return arr
+
+
+def dmrgc_default_options() -> Options:
+    o = Options()
+    _check(lib().dmrgc_default_options(C.byref(o)))
+    return o
+
+
+def dmrgc_create(n_qubits: int, rows: int, cols: int, chi: int, options: Options | None = None):
+    g = Grid(rows, cols, 0)
+    h = C.c_void_p()
+    opt = options if options is not None else dmrgc_default_options()
+    _check(lib().dmrgc_create(n_qubits, C.byref(g), chi, C.byref(opt), C.byref(h)))
+    return h
+
+
+def dmrgc_apply_layer(ctx, layer) -> None:
+    gates = pack_gates(layer)
+    _check(lib().dmrgc_apply_layer(ctx, gates, len(layer)), ctx)
+
+
+def dmrgc_sweep(ctx, n_sweeps: int) -> float:
+    f = C.c_double()
+    _check(lib().dmrgc_sweep(ctx, n_sweeps, C.byref(f)), ctx)
+    return f.value
+
+
+def dmrgc_fidelity(ctx) -> tuple[float, float]:
+    lf, fd = C.c_double(), C.c_double()
+    _check(lib().dmrgc_fidelity(ctx, C.byref(lf), C.byref(fd)), ctx)
+    return lf.value, fd.value
+
+
+def dmrgc_amplitude(ctx, bits: np.ndarray) -> np.ndarray:
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    out = np.zeros((bits.shape[0], 2), dtype=np.float64)
+    _check(lib().dmrgc_amplitude(ctx, bits.ctypes.data, bits.shape[0], out.ctypes.data), ctx)
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def dmrgc_sample(ctx, count: int, seed: int, n_qubits: int) -> np.ndarray:
+    out = np.zeros((count, n_qubits), dtype=np.uint8)
+    _check(lib().dmrgc_sample(ctx, count, C.c_ulonglong(seed), out.ctypes.data), ctx)
+    return out
+
+
+def dmrgc_bond_dims(ctx, n_qubits: int) -> tuple[list[int], list[int]]:
+    a = np.zeros(max(n_qubits - 1, 1), dtype=np.int32)
+    b = np.zeros(max(n_qubits - 1, 1), dtype=np.int32)
+    _check(lib().dmrgc_bond_dims(ctx, a.ctypes.data, b.ctypes.data), ctx)
+    return a[:n_qubits - 1].tolist(), b[:n_qubits - 1].tolist()
+
+
+def dmrgc_get_mps(ctx, n_qubits: int) -> tuple[list[np.ndarray], int]:
+    size = lib().dmrgc_mps_size(ctx)
+    buf = np.zeros(2 * size, dtype=np.float64)
+    centre = C.c_int()
+    _check(lib().dmrgc_get_mps(ctx, buf.ctypes.data, C.byref(centre)), ctx)
+    bonds, _ = dmrgc_bond_dims(ctx, n_qubits)
+    chis = [1] + bonds + [1]
+    z = buf[0::2] + 1j * buf[1::2]
+    out, off = [], 0
+    for i in range(n_qubits):
+        n = chis[i] * 2 * chis[i + 1]
+        out.append(z[off:off + n].reshape(chis[i], 2, chis[i + 1]))
+        off += n
+    return out, centre.value
+
+
+def dmrgc_step_history(ctx) -> list[float]:
+    n = C.c_int()
+    _check(lib().dmrgc_step_history(ctx, None, 0, C.byref(n)), ctx)
+    f = np.zeros(max(n.value, 1))
+    _check(lib().dmrgc_step_history(ctx, f.ctypes.data, n.value, C.byref(n)), ctx)
+    return f[:n.value].tolist()
+
+
+def dmrgc_get_stats(ctx) -> dict:
+    s = Stats()
+    _check(lib().dmrgc_get_stats(ctx, C.byref(s)), ctx)
+    return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+def dmrgc_reset_stats(ctx) -> None:
+    _check(lib().dmrgc_reset_stats(ctx), ctx)
+
+
+def dmrgc_destroy(ctx) -> None:
+    if ctx:
+        lib().dmrgc_destroy(ctx)
+
+
+class Context:
+    """Owning handle around the C context (marshalling only)."""
+
+    def __init__(self, rows: int, cols: int, chi: int, precision: int = DMRGC_FP64,
+                 timing: bool = False, stream=None, **opts):
+        o = dmrgc_default_options()
+        o.precision = precision
+        o.timing = 1 if timing else 0
+        if stream is not None:
+            o.cuda_stream = C.c_void_p(int(stream))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.n = rows * cols
+        self.h = dmrgc_create(self.n, rows, cols, chi, o)
+
+    def apply_layer(self, layer):
+        dmrgc_apply_layer(self.h, layer)
+
+    def sweep(self, n_sweeps: int = 2) -> float:
+        return dmrgc_sweep(self.h, n_sweeps)
+
+    def fidelity(self):
+        return dmrgc_fidelity(self.h)
+
+    def amplitude(self, bits):
+        return dmrgc_amplitude(self.h, bits)
+
+    def sample(self, count: int, seed: int):
+        return dmrgc_sample(self.h, count, seed, self.n)
+
+    def bond_dims(self):
+        return dmrgc_bond_dims(self.h, self.n)
+
+    def get_mps(self):
+        return dmrgc_get_mps(self.h, self.n)
+
+    def history(self):
+        return dmrgc_step_history(self.h)
+
+    def stats(self):
+        return dmrgc_get_stats(self.h)
+
+    def reset_stats(self):
+        dmrgc_reset_stats(self.h)
+
+    def close(self):
+        if self.h:
+            dmrgc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,887 @@
+// C ABI and host orchestration of the compression step (Sec. IV.B).
+//
+// Data layout in device memory (row-major, complex interleaved):
+//   MPS site i          A_i[chi_i][2][chi_{i+1}]     (new state)  B_i (previous state)
+//   layer MPO site i    Wx_i[s][D_{i+1}][D_i][t]  and  Wy_i[s][D_i][D_{i+1}][t]
+//   left environment    L[a_new][w][b_old],  right environment R[c_new][w][b_old]
+//   X_i = L_{i-1} B_i W_i        [a][s][w'][b']   (cached per site)
+//   Y_i = R_{i+1} B_i W_i        [s][c][w][b]     (cached per site)
+//   theta at bond (i,i+1) = X_i Y_{i+1}^T   [(a s1)][(s2 c)]   (Eq. scalarproduct)
+// Every contraction is one batched complex GEMM; the truncated SVD is the
+// one-sided Jacobi kernel.  X_i computed in a left-to-right update is what the
+// next right-to-left pass needs at the same bond, and Y_{i+1} likewise the
+// other way round, so each update computes one of X / Y and reuses the other.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace dmrgc;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct EnvRef {
+  const void* p = nullptr;
+  int a = 1, w = 1, b = 1;   // [a][w][b]
+};
+
+enum TimeClass { TC_GEMM = 0, TC_SVD = 1, TC_MPO = 2, TC_OTHER = 3 };
+
+}  // namespace
+
+struct dmrgc_ctx {
+  int N = 0, chi = 0, rows = 0, cols = 0, m = 0;
+  dmrgc_options opt{};
+  cudaStream_t st = nullptr;
+  bool fp64 = true;
+  size_t esz = 16;
+  double sweep_cut = 1e-12, zip_cut = 1e-5;
+  int max_jsweeps = 40;
+  std::vector<int> order, site_of;
+  std::vector<DevBuf> A, B, Wx, Wy, XY, E;
+  std::vector<int> chiA, chiB, D;     // N+1 entries each
+  std::vector<char> xyk;
+  DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
+  DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d;
+  EnvRef L, R;
+  int phase = 0;           // 0 created, 1 guess ready / sweeping
+  int bond = 0, dir = -1;  // next update (bond, bond+1), dir -1 = right-to-left
+  int centre = 0;
+  double log_ft = 0.0, f_cur = 1.0;
+  std::vector<double> hist;
+  std::string err;
+  dmrgc_stats stats{};
+  struct Pend { int cls; cudaEvent_t a, b; double flops; };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  ~dmrgc_ctx();
+};
+
+namespace {
+
+dmrgc_status fail(dmrgc_ctx* c, dmrgc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(c, DMRGC_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define TRY(x)                          \
+  do {                                  \
+    dmrgc_status s_ = (x);              \
+    if (s_ != DMRGC_OK) return s_;      \
+  } while (0)
+
+dmrgc_status ensure(dmrgc_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return DMRGC_OK;
+  if (b.p) {
+    cudaStreamSynchronize(c->st);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(c, DMRGC_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  b.cap = want;
+  return DMRGC_OK;
+}
+
+// ---- timing
+
+cudaEvent_t take_event(dmrgc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Span {
+  dmrgc_ctx* c;
+  int cls;
+  double flops;
+  cudaEvent_t a = nullptr;
+  Span(dmrgc_ctx* c_, int cls_, double flops_ = 0) : c(c_), cls(cls_), flops(flops_) {
+    if (c->opt.timing) {
+      a = take_event(c);
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~Span() {
+    if (c->opt.timing) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->st);
+      c->pend.push_back({cls, a, b, flops});
+    }
+  }
+};
+
+void flush_timing(dmrgc_ctx* c) {
+  for (auto& p : c->pend) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    switch (p.cls) {
+      case TC_GEMM: c->stats.gemm_ms += ms; c->stats.gemm_flops += p.flops; break;
+      case TC_SVD: c->stats.svd_ms += ms; break;
+      case TC_MPO: c->stats.mpo_ms += ms; break;
+      default: c->stats.other_ms += ms; break;
+    }
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pend.clear();
+}
+
+dmrgc_status sync(dmrgc_ctx* c) {
+  CK(cudaStreamSynchronize(c->st));
+  flush_timing(c);
+  return DMRGC_OK;
+}
+
+// ---- GEMM dispatch
+
+dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
+  if (c->opt.precision == DMRGC_BF16X3 || c->opt.precision == DMRGC_TF32X3)
+    return fail(c, DMRGC_EINVAL, "tensor-core precision modes are not available in this build");
+  const double fl = 8.0 * g.M * (double)g.N * g.K * g.b1 * g.b2;
+  Span sp(c, TC_GEMM, fl);
+  CK(gemm_simt(g, c->fp64, c->st));
+  c->stats.gemm_launches++;
+  c->stats.kernel_launches++;
+  return DMRGC_OK;
+}
+
+// X[a][s][w'][b'] = L[a][w][b] B[b][t][b'] W[w][s][t][w']
+dmrgc_status make_x(dmrgc_ctx* c, const EnvRef& L, int site, DevBuf& out) {
+  const int a = L.a, dw = L.w, b = L.b;
+  const int bp = c->chiB[site + 1];
+  const int dout = c->D[site + 1];
+  if (dw != c->D[site] || b != c->chiB[site]) return fail(c, DMRGC_ESTATE, "make_x: shape mismatch");
+  TRY(ensure(c, c->T, (size_t)a * dw * 2 * bp * c->esz));
+  TRY(ensure(c, out, (size_t)a * 2 * dout * bp * c->esz));
+  GemmArgs g1;
+  g1.M = a * dw; g1.N = 2 * bp; g1.K = b;
+  g1.A = L.p; g1.lda = b; g1.opA = OP_N;
+  g1.B = c->B[site].p; g1.ldb = 2 * bp; g1.opB = OP_N;
+  g1.C = c->T.p; g1.ldc = 2 * bp;
+  TRY(gemm(c, g1));
+  GemmArgs g2;
+  g2.M = 2 * dout; g2.N = bp; g2.K = 2 * dw; g2.b1 = a;
+  g2.A = c->Wx[site].p; g2.lda = 2 * dw; g2.sA1 = 0; g2.opA = OP_N;
+  g2.B = c->T.p; g2.ldb = bp; g2.sB1 = (long long)dw * 2 * bp; g2.opB = OP_N;
+  g2.C = out.p; g2.ldc = bp; g2.sC1 = (long long)2 * dout * bp;
+  return gemm(c, g2);
+}
+
+// Y[s][c][w][b] = R[c][w''][b''] B[b][t][b''] W[w][s][t][w'']
+dmrgc_status make_y(dmrgc_ctx* c, const EnvRef& R, int site, DevBuf& out) {
+  const int cc = R.a, dout = R.w, bpp = R.b;
+  const int bl = c->chiB[site];
+  const int din = c->D[site];
+  if (dout != c->D[site + 1] || bpp != c->chiB[site + 1]) return fail(c, DMRGC_ESTATE, "make_y: shape mismatch");
+  TRY(ensure(c, c->bt, (size_t)2 * bl * bpp * c->esz));
+  {
+    Span sp(c, TC_OTHER);
+    CK(permute_phys_first(c->B[site].p, bl, bpp, c->bt.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  TRY(ensure(c, c->T, (size_t)cc * dout * 2 * bl * c->esz));
+  TRY(ensure(c, out, (size_t)2 * cc * din * bl * c->esz));
+  GemmArgs g1;
+  g1.M = cc * dout; g1.N = 2 * bl; g1.K = bpp;
+  g1.A = R.p; g1.lda = bpp; g1.opA = OP_N;
+  g1.B = c->bt.p; g1.ldb = bpp; g1.opB = OP_T;
+  g1.C = c->T.p; g1.ldc = 2 * bl;
+  TRY(gemm(c, g1));
+  GemmArgs g2;
+  g2.M = din; g2.N = bl; g2.K = 2 * dout; g2.b1 = 2; g2.b2 = cc;
+  g2.A = c->Wy[site].p; g2.lda = 2 * dout; g2.sA1 = (long long)din * 2 * dout; g2.sA2 = 0; g2.opA = OP_N;
+  g2.B = c->T.p; g2.ldb = bl; g2.sB1 = 0; g2.sB2 = (long long)dout * 2 * bl; g2.opB = OP_N;
+  g2.C = out.p; g2.ldc = bl; g2.sC1 = (long long)cc * din * bl; g2.sC2 = (long long)din * bl;
+  return gemm(c, g2);
+}
+
+double jacobi_tol(const dmrgc_ctx* c, int m) {
+  const double eps = c->fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+  return 8.0 * eps * std::sqrt((double)std::max(m, 1));
+}
+
+// Orthogonalise the columns of jw (m x n column-major), truncate; returns k, f.
+dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, int& k, double& f) {
+  TRY(ensure(c, c->jctl, jacobi_ctl_bytes()));
+  TRY(ensure(c, c->tres, trunc_bytes(n)));
+  {
+    Span sp(c, TC_SVD);
+    int launches = 0;
+    CK(jacobi_orthogonalize(c->jw.p, m, n, c->fp64, jacobi_tol(c, m), c->max_jsweeps, c->jctl.p,
+                            c->st, &launches));
+    CK(truncate_columns(c->jw.p, m, n, c->fp64, c->chi, rel_cut, squared, c->tres.p, c->st));
+    c->stats.svd_launches += launches + 2;
+    c->stats.kernel_launches += launches + 2;
+  }
+  struct { int count, gen; unsigned off[2]; int err, sweeps, pad[2]; } ctl{};
+  TruncResult tr{};
+  CK(cudaMemcpyAsync(&ctl, c->jctl.p, sizeof(ctl), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(&tr, c->tres.p, sizeof(tr), cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  if (ctl.err == DMRGC_ETIMEOUT) return fail(c, DMRGC_ETIMEOUT, "Jacobi SVD grid barrier timed out");
+  if (ctl.err == DMRGC_ENOCONV)
+    return fail(c, DMRGC_ENOCONV, "Jacobi SVD did not converge in " + std::to_string(c->max_jsweeps) + " sweeps");
+  if (tr.status != 0 || !std::isfinite(tr.f) || !(tr.f > 0))
+    return fail(c, DMRGC_ENUMERIC, "truncated SVD met a zero or non-finite spectrum");
+  k = tr.k;
+  f = tr.f;
+  return DMRGC_OK;
+}
+
+// theta[(a s1)][(s2 c)] = X_i Y_{i+1}^T
+dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
+  const int a = c->chiA[i], cc = c->chiA[i + 2];
+  const int kdim = c->D[i + 1] * c->chiB[i + 1];
+  mrow = 2 * a;
+  ncol = 2 * cc;
+  TRY(ensure(c, c->theta, (size_t)mrow * ncol * c->esz));
+  GemmArgs g;
+  g.M = mrow; g.N = ncol; g.K = kdim;
+  g.A = c->XY[i].p; g.lda = kdim; g.opA = OP_N;
+  g.B = c->XY[i + 1].p; g.ldb = kdim; g.opB = OP_T;
+  g.C = c->theta.p; g.ldc = ncol;
+  return gemm(c, g);
+}
+
+dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
+  // X_i from the running left environment
+  EnvRef L = c->L;
+  if (i == 0) { L.p = c->one.p; L.a = 1; L.w = 1; L.b = 1; }
+  TRY(make_x(c, L, i, c->XY[i]));
+  c->xyk[i] = 'X';
+  if (c->xyk[i + 1] != 'Y') return fail(c, DMRGC_ESTATE, "right cache missing");
+  int mrow, ncol;
+  TRY(form_theta(c, i, mrow, ncol));
+  TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+  {
+    Span sp(c, TC_OTHER);
+    CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  int k;
+  double f;
+  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, k, f));
+  TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
+  {
+    Span sp(c, TC_SVD);
+    CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
+  GemmArgs g;   // A_{i+1} = A_i^+ theta / |S_k|
+  g.M = k; g.N = ncol; g.K = mrow;
+  g.A = c->A[i].p; g.lda = k; g.opA = OP_C;
+  g.B = c->theta.p; g.ldb = ncol; g.opB = OP_N;
+  g.C = c->A[i + 1].p; g.ldc = ncol;
+  g.alpha_re = 1.0 / std::sqrt(f);
+  TRY(gemm(c, g));
+  c->chiA[i + 1] = k;
+  // L_i = A_i^+ X_i
+  const int kdim = c->D[i + 1] * c->chiB[i + 1];
+  TRY(ensure(c, c->envL, (size_t)k * kdim * c->esz));
+  GemmArgs h;
+  h.M = k; h.N = kdim; h.K = mrow;
+  h.A = c->A[i].p; h.lda = k; h.opA = OP_C;
+  h.B = c->XY[i].p; h.ldb = kdim; h.opB = OP_N;
+  h.C = c->envL.p; h.ldc = kdim;
+  TRY(gemm(c, h));
+  c->L.p = c->envL.p; c->L.a = k; c->L.w = c->D[i + 1]; c->L.b = c->chiB[i + 1];
+  c->f_cur = f;
+  c->hist.push_back(f);
+  c->centre = i + 1;
+  c->stats.updates++;
+  return DMRGC_OK;
+}
+
+dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
+  EnvRef R = c->R;
+  if (i + 1 == c->N - 1) { R.p = c->one.p; R.a = 1; R.w = 1; R.b = 1; }
+  TRY(make_y(c, R, i + 1, c->XY[i + 1]));
+  c->xyk[i + 1] = 'Y';
+  if (c->xyk[i] != 'X') return fail(c, DMRGC_ESTATE, "left cache missing");
+  int mrow, ncol;
+  TRY(form_theta(c, i, mrow, ncol));
+  TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+  {
+    Span sp(c, TC_OTHER);
+    CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  int k;
+  double f;
+  // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
+  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, k, f));
+  TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
+  {
+    Span sp(c, TC_SVD);
+    CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
+  GemmArgs g;   // A_i = theta A_{i+1}^+ / |S_k|
+  g.M = mrow; g.N = k; g.K = ncol;
+  g.A = c->theta.p; g.lda = ncol; g.opA = OP_N;
+  g.B = c->A[i + 1].p; g.ldb = ncol; g.opB = OP_C;
+  g.C = c->A[i].p; g.ldc = k;
+  g.alpha_re = 1.0 / std::sqrt(f);
+  TRY(gemm(c, g));
+  c->chiA[i + 1] = k;
+  const int kdim = c->D[i + 1] * c->chiB[i + 1];
+  TRY(ensure(c, c->envR, (size_t)k * kdim * c->esz));
+  GemmArgs h;   // R_{i+1} = conj(A_{i+1}) Y_{i+1}
+  h.M = k; h.N = kdim; h.K = ncol;
+  h.A = c->A[i + 1].p; h.lda = ncol; h.opA = OP_R;
+  h.B = c->XY[i + 1].p; h.ldb = kdim; h.opB = OP_N;
+  h.C = c->envR.p; h.ldc = kdim;
+  TRY(gemm(c, h));
+  c->R.p = c->envR.p; c->R.a = k; c->R.w = c->D[i + 1]; c->R.b = c->chiB[i + 1];
+  c->f_cur = f;
+  c->hist.push_back(f);
+  c->centre = i;
+  c->stats.updates++;
+  return DMRGC_OK;
+}
+
+// Gram matrix (column-major) of the rows of M (r x K row-major): G = M M^+
+dmrgc_status gram_colmajor(dmrgc_ctx* c, const void* M, int r, int kdim) {
+  TRY(ensure(c, c->jw, (size_t)r * r * c->esz));
+  GemmArgs g;   // buffer[r1][r2] = sum_k conj(M[r1][k]) M[r2][k] = G[r2][r1]
+  g.M = r; g.N = r; g.K = kdim;
+  g.A = M; g.lda = kdim; g.opA = OP_R;
+  g.B = M; g.ldb = kdim; g.opB = OP_T;
+  g.C = c->jw.p; g.ldc = r;
+  return gemm(c, g);
+}
+
+dmrgc_status set_identity_site(dmrgc_ctx* c, DevBuf& dst, int r) {
+  TRY(ensure(c, dst, (size_t)r * r * c->esz));
+  Span sp(c, TC_OTHER);
+  CK(set_identity(dst.p, r, c->fp64, c->st));
+  c->stats.kernel_launches++;
+  return DMRGC_OK;
+}
+
+// Zip-up initial guess from both ends towards the centre site m.
+dmrgc_status zip_guess(dmrgc_ctx* c) {
+  const int N = c->N, m = c->m;
+  c->chiA.assign(N + 1, 1);
+  // left part
+  EnvRef L;
+  L.p = c->one.p; L.a = 1; L.w = 1; L.b = 1;
+  for (int i = 0; i < m; ++i) {
+    TRY(make_x(c, L, i, c->XY[i]));
+    c->xyk[i] = 'X';
+    const int r = 2 * c->chiA[i];
+    const int kdim = c->D[i + 1] * c->chiB[i + 1];
+    if (r <= c->chi) {
+      TRY(set_identity_site(c, c->A[i], r));
+      c->chiA[i + 1] = r;
+      L.p = c->XY[i].p; L.a = r; L.w = c->D[i + 1]; L.b = c->chiB[i + 1];
+      continue;
+    }
+    TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
+    int k;
+    double f;
+    TRY(svd_columns(c, r, r, c->zip_cut, true, k, f));
+    TRY(ensure(c, c->A[i], (size_t)r * k * c->esz));
+    {
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, r, r, k, c->tres.p, true, 0, c->A[i].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    c->chiA[i + 1] = k;
+    TRY(ensure(c, c->envL, (size_t)k * kdim * c->esz));
+    GemmArgs h;
+    h.M = k; h.N = kdim; h.K = r;
+    h.A = c->A[i].p; h.lda = k; h.opA = OP_C;
+    h.B = c->XY[i].p; h.ldb = kdim; h.opB = OP_N;
+    h.C = c->envL.p; h.ldc = kdim;
+    TRY(gemm(c, h));
+    L.p = c->envL.p; L.a = k; L.w = c->D[i + 1]; L.b = c->chiB[i + 1];
+  }
+  // right part
+  EnvRef R;
+  R.p = c->one.p; R.a = 1; R.w = 1; R.b = 1;
+  for (int i = N - 1; i > m; --i) {
+    TRY(make_y(c, R, i, c->XY[i]));
+    c->xyk[i] = 'Y';
+    const int r = 2 * c->chiA[i + 1];
+    const int kdim = c->D[i] * c->chiB[i];
+    if (r <= c->chi) {
+      TRY(set_identity_site(c, c->A[i], r));
+      c->chiA[i] = r;
+      R.p = c->XY[i].p; R.a = r; R.w = c->D[i]; R.b = c->chiB[i];
+      continue;
+    }
+    TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
+    int k;
+    double f;
+    TRY(svd_columns(c, r, r, c->zip_cut, true, k, f));
+    TRY(ensure(c, c->A[i], (size_t)k * r * c->esz));
+    {
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, r, r, k, c->tres.p, true, 1, c->A[i].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    c->chiA[i] = k;
+    TRY(ensure(c, c->envR, (size_t)k * kdim * c->esz));
+    GemmArgs h;
+    h.M = k; h.N = kdim; h.K = r;
+    h.A = c->A[i].p; h.lda = r; h.opA = OP_R;
+    h.B = c->XY[i].p; h.ldb = kdim; h.opB = OP_N;
+    h.C = c->envR.p; h.ldc = kdim;
+    TRY(gemm(c, h));
+    R.p = c->envR.p; R.a = k; R.w = c->D[i]; R.b = c->chiB[i];
+  }
+  // centre: C = X_m R_{m+1}^T, normalised
+  TRY(make_x(c, L, m, c->XY[m]));
+  c->xyk[m] = 'X';
+  const int mrow = 2 * c->chiA[m], ncol = c->chiA[m + 1];
+  const int kdim = c->D[m + 1] * c->chiB[m + 1];
+  TRY(ensure(c, c->A[m], (size_t)mrow * ncol * c->esz));
+  GemmArgs g;
+  g.M = mrow; g.N = ncol; g.K = kdim;
+  g.A = c->XY[m].p; g.lda = kdim; g.opA = OP_N;
+  g.B = R.p; g.ldb = kdim; g.opB = OP_T;
+  g.C = c->A[m].p; g.ldc = ncol;
+  TRY(gemm(c, g));
+  TRY(ensure(c, c->scal, 64));
+  {
+    Span sp(c, TC_OTHER);
+    CK(sum_abs2(c->A[m].p, (long long)mrow * ncol, c->fp64, (double*)c->scal.p, c->st));
+    CK(scale_inplace(c->A[m].p, (long long)mrow * ncol, (const double*)c->scal.p, c->fp64, c->st));
+    c->stats.kernel_launches += 2;
+  }
+  double nrm2 = 0;
+  CK(cudaMemcpyAsync(&nrm2, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  if (!(nrm2 > 0) || !std::isfinite(nrm2))
+    return fail(c, DMRGC_ENUMERIC, "zip-up guess has zero overlap with the target state");
+  c->f_cur = nrm2;
+  c->L = L;
+  c->R = R;
+  c->centre = m;
+  return DMRGC_OK;
+}
+
+// ---- layer MPO plan
+
+dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
+  const int N = c->N;
+  std::vector<GateDev> gd(n_gates);
+  for (int g = 0; g < n_gates; ++g) {
+    const dmrgc_gate& x = gates[g];
+    if (x.q0 < 0 || x.q0 >= N || x.q1 >= N || x.q1 < -1 || x.q1 == x.q0)
+      return fail(c, DMRGC_EINVAL, "gate " + std::to_string(g) + " has invalid qubits");
+    for (int j = 0; j < 32; ++j)
+      if (!std::isfinite(x.mat[j])) return fail(c, DMRGC_EINVAL, "gate " + std::to_string(g) + " is not finite");
+    GateDev d{};
+    const int s0 = c->site_of[x.q0];
+    if (x.q1 < 0) { d.p = s0; d.q = -1; d.swap = 0; }
+    else {
+      const int s1 = c->site_of[x.q1];
+      d.p = std::min(s0, s1); d.q = std::max(s0, s1); d.swap = s0 > s1 ? 1 : 0;
+    }
+    std::memcpy(d.mat, x.mat, sizeof(d.mat));
+    gd[g] = d;
+  }
+  const int ng = std::max(n_gates, 1);
+  TRY(ensure(c, c->gates_d, sizeof(GateDev) * ng));
+  TRY(ensure(c, c->rank_d, sizeof(int) * ng));
+  TRY(ensure(c, c->fa_d, sizeof(double2) * 16 * ng));
+  TRY(ensure(c, c->fb_d, sizeof(double2) * 16 * ng));
+  std::vector<int> rank(ng, 0);
+  if (n_gates > 0) {
+    CK(cudaMemcpyAsync(c->gates_d.p, gd.data(), sizeof(GateDev) * n_gates, cudaMemcpyHostToDevice, c->st));
+    {
+      Span sp(c, TC_MPO);
+      CK(gate_split((const GateDev*)c->gates_d.p, n_gates, (int*)c->rank_d.p, (double2*)c->fa_d.p,
+                    (double2*)c->fb_d.p, c->st));
+      c->stats.kernel_launches++;
+    }
+    CK(cudaMemcpyAsync(rank.data(), c->rank_d.p, sizeof(int) * n_gates, cudaMemcpyDeviceToHost, c->st));
+    TRY(sync(c));
+  }
+  // legs crossing each cut (between site i-1 and i), in gate order
+  std::vector<std::vector<int>> legs(N + 1);
+  c->D.assign(N + 1, 1);
+  for (int cut = 1; cut < N; ++cut) {
+    double d = 1;
+    for (int g = 0; g < n_gates; ++g)
+      if (gd[g].q >= 0 && gd[g].p < cut && cut <= gd[g].q && rank[g] > 0) {
+        legs[cut].push_back(g);
+        d *= rank[g];
+      }
+    if (d > 4096 || legs[cut].size() > 24)
+      return fail(c, DMRGC_EINVAL, "layer MPO bond at cut " + std::to_string(cut) + " exceeds 4096");
+    c->D[cut] = (int)d;
+  }
+  // plan table
+  std::vector<int> tab;
+  std::vector<SitePlan> plans(N);
+  for (int i = 0; i < N; ++i) {
+    const std::vector<int>& in = legs[i];
+    const std::vector<int>& out = legs[i + 1];
+    SitePlan sp{};
+    sp.d_in = c->D[i];
+    sp.d_out = c->D[i + 1];
+    sp.n_in = (int)in.size();
+    sp.n_out = (int)out.size();
+    sp.off = (long long)tab.size();
+    for (int g : in) {
+      int po = -1;
+      for (size_t j = 0; j < out.size(); ++j)
+        if (out[j] == g) po = (int)j;
+      tab.push_back(g); tab.push_back(rank[g]); tab.push_back(po);
+    }
+    for (int g : out) { tab.push_back(g); tab.push_back(rank[g]); }
+    int nops = 0;
+    for (int g = 0; g < n_gates; ++g) {
+      if (gd[g].q < 0) {
+        if (gd[g].p == i) { tab.push_back(0); tab.push_back(g); tab.push_back(0); ++nops; }
+      } else if (gd[g].p == i) {
+        int j = (int)(std::find(out.begin(), out.end(), g) - out.begin());
+        tab.push_back(1); tab.push_back(g); tab.push_back(j); ++nops;
+      } else if (gd[g].q == i) {
+        int j = (int)(std::find(in.begin(), in.end(), g) - in.begin());
+        tab.push_back(2); tab.push_back(g); tab.push_back(j); ++nops;
+      }
+    }
+    sp.n_ops = nops;
+    plans[i] = sp;
+  }
+  TRY(ensure(c, c->plan_d, sizeof(int) * std::max<size_t>(tab.size(), 1)));
+  if (!tab.empty())
+    CK(cudaMemcpyAsync(c->plan_d.p, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, c->st));
+  for (int i = 0; i < N; ++i) {
+    const size_t bytes = (size_t)plans[i].d_in * 4 * plans[i].d_out * c->esz;
+    TRY(ensure(c, c->Wx[i], bytes));
+    TRY(ensure(c, c->Wy[i], bytes));
+    Span sp(c, TC_MPO);
+    CK(build_site_mpo((const int*)c->plan_d.p, plans[i], (const GateDev*)c->gates_d.p,
+                      (const double2*)c->fa_d.p, (const double2*)c->fb_d.p, c->Wx[i].p, c->Wy[i].p,
+                      c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  return DMRGC_OK;
+}
+
+}  // namespace
+
+dmrgc_ctx::~dmrgc_ctx() {
+  auto fr = [](DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; };
+  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E})
+    for (auto& b : *v) fr(b);
+  for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
+                    &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d})
+    fr(*b);
+  for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+extern "C" {
+
+dmrgc_status dmrgc_default_options(dmrgc_options* opt) {
+  if (!opt) return DMRGC_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = DMRGC_FP64;
+  opt->svd_mode = 0;
+  opt->max_jacobi_sweeps = 40;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const dmrgc_options* opt,
+                          dmrgc_ctx** out) {
+  if (!out || !grid) return DMRGC_EINVAL;
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 4096 || grid->rows < 1 || grid->cols < 1 ||
+      grid->rows * grid->cols != n_qubits || grid->order != 0 || chi < 1 || chi > 4096)
+    return DMRGC_EINVAL;
+  dmrgc_ctx* c = new (std::nothrow) dmrgc_ctx();
+  if (!c) return DMRGC_ENOMEM;
+  if (opt) c->opt = *opt; else dmrgc_default_options(&c->opt);
+  if (c->opt.precision < 0 || c->opt.precision > 3 || c->opt.svd_mode != 0) { delete c; return DMRGC_EINVAL; }
+  c->N = n_qubits; c->chi = chi; c->rows = grid->rows; c->cols = grid->cols; c->m = n_qubits / 2;
+  c->st = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
+  c->fp64 = c->opt.precision == DMRGC_FP64;
+  c->esz = c->fp64 ? 16 : 8;
+  c->sweep_cut = c->opt.sweep_rel_cutoff > 0 ? c->opt.sweep_rel_cutoff : (c->fp64 ? 1e-12 : 1e-6);
+  c->zip_cut = c->opt.zip_rel_cutoff > 0 ? c->opt.zip_rel_cutoff : (c->fp64 ? 1e-5 : 1e-3);
+  c->max_jsweeps = c->opt.max_jacobi_sweeps > 0 ? c->opt.max_jacobi_sweeps : 40;
+  for (int col = 0; col < c->cols; ++col)
+    for (int k = 0; k < c->rows; ++k) {
+      const int r = (col % 2 == 0) ? k : c->rows - 1 - k;
+      c->order.push_back(r * c->cols + col);
+    }
+  c->site_of.assign(n_qubits, 0);
+  for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
+  c->A.resize(n_qubits); c->B.resize(n_qubits); c->Wx.resize(n_qubits); c->Wy.resize(n_qubits);
+  c->XY.resize(n_qubits); c->E.resize(n_qubits); c->xyk.assign(n_qubits, 0);
+  c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);
+  dmrgc_status s = ensure(c, c->one, 64);
+  if (s == DMRGC_OK) {
+    cudaError_t e = set_scalar_one(c->one.p, c->fp64, c->st);
+    for (int i = 0; i < n_qubits && e == cudaSuccess && s == DMRGC_OK; ++i) {
+      s = ensure(c, c->B[i], 2 * c->esz);
+      if (s == DMRGC_OK) {
+        e = cudaMemsetAsync(c->B[i].p, 0, 2 * c->esz, c->st);
+        if (e == cudaSuccess) e = set_scalar_one(c->B[i].p, c->fp64, c->st);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = fail(c, DMRGC_ECUDA, cudaGetErrorString(e));
+  }
+  if (s != DMRGC_OK) { delete c; return s; }
+  c->phase = 0;
+  c->centre = 0;
+  *out = c;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
+  if (!c) return DMRGC_EINVAL;
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(c, DMRGC_EINVAL, "bad gate list");
+  if (c->phase == 1) {   // commit the previous step: its state becomes |Psi_Q(D)>
+    c->log_ft += std::log(c->f_cur);
+    std::swap(c->A, c->B);
+    c->chiB = c->chiA;
+  }
+  c->hist.clear();
+  TRY(build_mpo(c, gates, n_gates));
+  std::fill(c->xyk.begin(), c->xyk.end(), 0);
+  TRY(zip_guess(c));
+  c->bond = c->m - 1;
+  c->dir = -1;
+  c->phase = 1;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_sweep(dmrgc_ctx* c, int n_sweeps, double* f_last) {
+  if (!c) return DMRGC_EINVAL;
+  if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep before dmrgc_apply_layer");
+  if (n_sweeps < 0) return fail(c, DMRGC_EINVAL, "n_sweeps < 0");
+  const long long total = (long long)n_sweeps * (c->N - 1);
+  for (long long u = 0; u < total; ++u) {
+    if (c->bond < 0) { c->bond = 0; c->dir = +1; }
+    const int b = c->bond;
+    if (c->dir < 0) {
+      TRY(update_rtl(c, b));
+      if (b == 0) c->dir = +1; else c->bond = b - 1;
+    } else {
+      TRY(update_ltr(c, b));
+      if (b == c->N - 2) c->dir = -1; else c->bond = b + 1;
+    }
+  }
+  TRY(sync(c));
+  if (f_last) *f_last = c->f_cur;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_fidelity(dmrgc_ctx* c, double* log_F_tilde, double* f_delta_last) {
+  if (!c) return DMRGC_EINVAL;
+  double lf = c->log_ft;
+  if (c->phase == 1) lf += std::log(c->f_cur);
+  if (log_F_tilde) *log_F_tilde = lf;
+  if (f_delta_last) *f_delta_last = c->phase == 1 ? c->f_cur : 1.0;
+  return DMRGC_OK;
+}
+
+static std::vector<DevBuf>& current_state(dmrgc_ctx* c, std::vector<int>*& bonds) {
+  if (c->phase == 1) { bonds = &c->chiA; return c->A; }
+  bonds = &c->chiB;
+  return c->B;
+}
+
+static dmrgc_status upload_tables(dmrgc_ctx* c, std::vector<DevBuf>& st, const std::vector<int>& bonds,
+                                  int& maxb) {
+  const int N = c->N;
+  std::vector<const void*> ptrs(N);
+  for (int i = 0; i < N; ++i) ptrs[i] = st[i].p;
+  std::vector<int> bt(bonds.begin(), bonds.end());
+  maxb = *std::max_element(bt.begin(), bt.end());
+  bt.push_back(maxb);
+  TRY(ensure(c, c->ptrs_d, sizeof(void*) * 2 * N));
+  TRY(ensure(c, c->bonds_d, sizeof(int) * (N + 2)));
+  TRY(ensure(c, c->order_d, sizeof(int) * N));
+  CK(cudaMemcpyAsync(c->ptrs_d.p, ptrs.data(), sizeof(void*) * N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->bonds_d.p, bt.data(), sizeof(int) * (N + 2), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->order_d.p, c->order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
+  if (!c) return DMRGC_EINVAL;
+  if (count < 0 || (count > 0 && (!bits || !out_re_im))) return fail(c, DMRGC_EINVAL, "bad amplitude arguments");
+  if (count == 0) return DMRGC_OK;
+  if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
+  for (long long j = 0; j < count * c->N; ++j)
+    if (bits[j] > 1) return fail(c, DMRGC_EINVAL, "bits must be 0 or 1");
+  std::vector<int>* bonds;
+  auto& st = current_state(c, bonds);
+  int maxb;
+  TRY(upload_tables(c, st, *bonds, maxb));
+  TRY(ensure(c, c->bits_d, (size_t)count * c->N));
+  TRY(ensure(c, c->out_d, (size_t)count * sizeof(double2)));
+  CK(cudaMemcpyAsync(c->bits_d.p, bits, (size_t)count * c->N, cudaMemcpyHostToDevice, c->st));
+  {
+    Span sp(c, TC_OTHER);
+    CK(amplitudes((const void* const*)c->ptrs_d.p, (const int*)c->bonds_d.p, (const int*)c->order_d.p,
+                  c->N, maxb, (const unsigned char*)c->bits_d.p, count, (double2*)c->out_d.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(out_re_im, c->out_d.p, (size_t)count * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  return sync(c);
+}
+
+dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed, unsigned char* out_bits) {
+  if (!c) return DMRGC_EINVAL;
+  if (count < 0 || (count > 0 && !out_bits)) return fail(c, DMRGC_EINVAL, "bad sample arguments");
+  if (count == 0) return DMRGC_OK;
+  if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
+  std::vector<int>* bonds;
+  auto& st = current_state(c, bonds);
+  const int N = c->N;
+  const int centre = c->phase == 1 ? c->centre : 0;   // product state: any centre works
+  // norm matrices E_i of sites > i for i < centre
+  std::vector<const void*> eptr(N, nullptr);
+  for (int i = centre - 1; i >= 0; --i) {
+    const int a = (*bonds)[i + 1], b = (*bonds)[i + 2];
+    TRY(ensure(c, c->E[i], (size_t)a * a * c->esz));
+    TRY(ensure(c, c->T, (size_t)a * 2 * b * c->esz));
+    const void* An = st[i + 1].p;
+    const void* Tsrc = An;
+    if (i + 1 < centre) {   // T[(a s)][b] = A_{i+1}[(a s)][b'] E_{i+1}[b'][b]
+      GemmArgs g;
+      g.M = 2 * a; g.N = b; g.K = b;
+      g.A = An; g.lda = b; g.opA = OP_N;
+      g.B = c->E[i + 1].p; g.ldb = b; g.opB = OP_N;
+      g.C = c->T.p; g.ldc = b;
+      TRY(gemm(c, g));
+      Tsrc = c->T.p;
+    }
+    GemmArgs h;   // E_i[a][a'] = sum_{(s b)} T[a][(s b)] conj(A_{i+1}[a'][(s b)])
+    h.M = a; h.N = a; h.K = 2 * b;
+    h.A = Tsrc; h.lda = 2 * b; h.opA = OP_N;
+    h.B = An; h.ldb = 2 * b; h.opB = OP_C;
+    h.C = c->E[i].p; h.ldc = a;
+    TRY(gemm(c, h));
+    eptr[i] = c->E[i].p;
+  }
+  int maxb;
+  TRY(upload_tables(c, st, *bonds, maxb));
+  CK(cudaMemcpyAsync((char*)c->ptrs_d.p + sizeof(void*) * N, eptr.data(), sizeof(void*) * N,
+                     cudaMemcpyHostToDevice, c->st));
+  TRY(ensure(c, c->bits_d, (size_t)count * N));
+  {
+    Span sp(c, TC_OTHER);
+    CK(sample_bits((const void* const*)c->ptrs_d.p, (const void* const*)c->ptrs_d.p + N,
+                   (const int*)c->bonds_d.p, (const int*)c->order_d.p, N, centre, maxb, seed, count,
+                   (unsigned char*)c->bits_d.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(out_bits, c->bits_d.p, (size_t)count * N, cudaMemcpyDeviceToHost, c->st));
+  return sync(c);
+}
+
+dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* c, int* mps_bonds, int* mpo_bonds) {
+  if (!c) return DMRGC_EINVAL;
+  const std::vector<int>& b = c->phase == 1 ? c->chiA : c->chiB;
+  for (int i = 0; i + 1 < c->N; ++i) {
+    if (mps_bonds) mps_bonds[i] = b[i + 1];
+    if (mpo_bonds) mpo_bonds[i] = c->D[i + 1];
+  }
+  return DMRGC_OK;
+}
+
+long long dmrgc_mps_size(const dmrgc_ctx* c) {
+  if (!c) return -1;
+  const std::vector<int>& b = c->phase == 1 ? c->chiA : c->chiB;
+  long long s = 0;
+  for (int i = 0; i < c->N; ++i) s += 2LL * b[i] * b[i + 1];
+  return s;
+}
+
+dmrgc_status dmrgc_get_mps(const dmrgc_ctx* cc, double* out_re_im, int* centre) {
+  dmrgc_ctx* c = const_cast<dmrgc_ctx*>(cc);
+  if (!c || !out_re_im) return DMRGC_EINVAL;
+  std::vector<int>* bonds;
+  auto& st = current_state(c, bonds);
+  long long off = 0;
+  for (int i = 0; i < c->N; ++i) {
+    const long long n = 2LL * (*bonds)[i] * (*bonds)[i + 1];
+    TRY(ensure(c, c->stage_d, (size_t)n * sizeof(double2)));
+    CK(to_complex128(st[i].p, n, c->fp64, (double2*)c->stage_d.p, c->st));
+    CK(cudaMemcpyAsync(out_re_im + 2 * off, c->stage_d.p, (size_t)n * sizeof(double2),
+                       cudaMemcpyDeviceToHost, c->st));
+    TRY(sync(c));
+    off += n;
+  }
+  if (centre) *centre = c->phase == 1 ? c->centre : 0;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_step_history(const dmrgc_ctx* c, double* f, int cap, int* count) {
+  if (!c) return DMRGC_EINVAL;
+  const int n = (int)c->hist.size();
+  if (f)
+    for (int i = 0; i < n && i < cap; ++i) f[i] = c->hist[i];
+  if (count) *count = n;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_get_stats(const dmrgc_ctx* c, dmrgc_stats* out) {
+  if (!c || !out) return DMRGC_EINVAL;
+  *out = c->stats;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_reset_stats(dmrgc_ctx* c) {
+  if (!c) return DMRGC_EINVAL;
+  dmrgc_status s = sync(c);
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  return s;
+}
+
+const char* dmrgc_last_error(const dmrgc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void dmrgc_destroy(dmrgc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  delete c;
+}
+
+}  // extern "C"

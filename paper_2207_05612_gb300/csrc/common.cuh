@@ -1,0 +1,131 @@
+// Shared declarations of the dmrgc CUDA library (device helpers, kernel
+// launchers, the context).  Complex numbers are stored as interleaved
+// (re, im) pairs: double2 in FP64 mode, float2 in the complex64 modes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrgc.h"
+
+namespace dmrgc {
+
+// ------------------------------------------------------------------ complex
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { using T = double2; };
+template <> struct cplx<float> { using T = float2; };
+
+template <typename C2>
+__host__ __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+  return C2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C2>
+__host__ __device__ __forceinline__ C2 cconj(C2 a) { return C2{a.x, -a.y}; }
+template <typename C2>
+__host__ __device__ __forceinline__ C2 cadd(C2 a, C2 b) { return C2{a.x + b.x, a.y + b.y}; }
+
+// ------------------------------------------------------------------- GEMM
+
+// Row-major batched complex GEMM:  C[b] = alpha * op(A[b]) * op(B[b]) (+ beta*C[b])
+// op(A)[m][k]: OP_N A[m*lda+k], OP_T A[k*lda+m], OP_C conj(A[k*lda+m]), OP_R conj(A[m*lda+k])
+// op(B)[k][n]: OP_N B[k*ldb+n], OP_T B[n*ldb+k], OP_C conj(B[n*ldb+k]), OP_R conj(B[k*ldb+n])
+// batch index b = i1*b2 + i2 with element offsets i1*s?1 + i2*s?2.
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_R = 3 };
+
+struct GemmArgs {
+  int M = 0, N = 0, K = 0;
+  int b1 = 1, b2 = 1;
+  const void* A = nullptr; long long lda = 0, sA1 = 0, sA2 = 0; int opA = OP_N;
+  const void* B = nullptr; long long ldb = 0, sB1 = 0, sB2 = 0; int opB = OP_N;
+  void* C = nullptr; long long ldc = 0, sC1 = 0, sC2 = 0;
+  double alpha_re = 1.0, alpha_im = 0.0;
+  int beta_one = 0;   // 1: accumulate into C
+};
+
+cudaError_t gemm_simt(const GemmArgs& g, bool fp64, cudaStream_t st);
+
+// --------------------------------------------------------------------- SVD
+
+// One-sided (Hestenes) Jacobi on the columns of G (column-major, m x n,
+// leading dimension m), in place: on return G = W = G0 V with mutually
+// orthogonal columns.  ctl must point to device scratch of jacobi_ctl_bytes().
+size_t jacobi_ctl_bytes();
+cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
+                                 void* ctl, cudaStream_t st, int* launches);
+
+// Column norms of W, sort descending, truncation rank.  Writes into res (device):
+// res->k, res->f = sum_{j<k} s_j^2, res->perm[j], res->s[j] (sorted).
+// squared: the column norms are s^2 (Gram input) -> s = sqrt(norm).
+struct TruncResult {
+  int k;
+  int n;
+  int status;     // 0 ok, 5 = numeric (NaN/zero)
+  int pad;
+  double f;       // sum of kept s^2
+  double norm2;   // sum of all s^2
+};
+size_t trunc_bytes(int n);  // TruncResult followed by double s[n], int perm[n]
+cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, double rel_cut,
+                             bool squared, void* res, cudaStream_t st);
+
+// Gather kept columns into MPS layouts.  mode:
+//  0: out[row*k + j] = W[row + perm[j]*m] / scale_j            (U_k row-major [m][k])
+//  1: out[j*m + row] = W[row + perm[j]*m] / scale_j            (U_k^T, [k][m])
+//  2: out[j*m + row] = conj(W[row + perm[j]*m]) / scale_j      (V_k^+, [k][m])
+// scale_j = s_j (or s_j^2 when squared: Gram input, where the column norm is s^2).
+cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void* res,
+                           bool squared, int mode, void* out, bool fp64, cudaStream_t st);
+
+// ---------------------------------------------------------------- MPO build
+
+struct GateDev {   // device copy of one gate, already in site order
+  int p, q;        // sites, p < q; q = -1 for a one-qubit gate
+  int swap;        // 1: the given matrix lists q1's index first
+  int pad;
+  double mat[32];
+};
+// Operator Schmidt split of every two-qubit gate (App. A splitting):
+// U = sum_k A_k (x) B_k, k < rank; A, B stored [gate][4][2][2] complex128.
+cudaError_t gate_split(const GateDev* gates, int n_gates, int* rank, double2* fa, double2* fb,
+                       cudaStream_t st);
+
+// Build W_i of one site from its plan: writes Wx[s][w_out][w_in][t] and
+// Wy[s][w_in][w_out][t] in the working precision.
+struct SitePlan {
+  int d_in, d_out;
+  int n_in, n_out, n_ops, pad;
+  long long off;   // offset (ints) into the plan table of this site's records
+};
+cudaError_t build_site_mpo(const int* plan_tab, SitePlan sp, const GateDev* gates, const double2* fa,
+                           const double2* fb, void* wx, void* wy, bool fp64, cudaStream_t st);
+
+// ------------------------------------------------------------------- misc
+
+cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void* dst, bool fp64,
+                           cudaStream_t st);   // dst[c*rows + r] = op(src[r*cols + c])
+cudaError_t copy_conj(const void* src, long long n, void* dst, bool fp64, cudaStream_t st);
+cudaError_t permute_phys_first(const void* src, int a, int b, void* dst, bool fp64,
+                               cudaStream_t st);  // [a][2][b] -> [2][a][b]
+cudaError_t set_identity(void* dst, int n, bool fp64, cudaStream_t st);  // n x n
+cudaError_t set_scalar_one(void* dst, bool fp64, cudaStream_t st);
+cudaError_t sum_abs2(const void* x, long long n, bool fp64, double* out_dev, cudaStream_t st);
+cudaError_t scale_inplace(void* x, long long n, const double* inv_norm_dev, bool fp64,
+                          cudaStream_t st);
+cudaError_t to_complex128(const void* src, long long n, bool fp64, double2* dst, cudaStream_t st);
+
+// --------------------------------------------------------------- read-outs
+
+cudaError_t amplitudes(const void* const* sites, const int* bonds, const int* order, int n_sites,
+                       int max_bond, const unsigned char* bits, long long count, double2* out,
+                       bool fp64, cudaStream_t st);
+cudaError_t sample_bits(const void* const* sites, const void* const* emat, const int* bonds,
+                        const int* order, int n_sites, int centre, int max_bond,
+                        unsigned long long seed, long long count, unsigned char* out, bool fp64,
+                        cudaStream_t st);
+
+}  // namespace dmrgc

@@ -1,0 +1,159 @@
+// Small layout and reduction kernels: transposed / conjugated copies, the
+// physical-index-first permutation of MPS tensors, identities, norms, scaling.
+#include "common.cuh"
+
+namespace dmrgc {
+namespace {
+
+inline int blocks_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 65536) b = 65536;
+  return b < 1 ? 1 : (int)b;
+}
+
+template <typename C2>
+__global__ void transpose_kernel(const C2* __restrict__ src, int rows, int cols, int conj,
+                                 C2* __restrict__ dst) {
+  __shared__ C2 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = by + j, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[j][threadIdx.x] = src[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = bx + j, r = by + threadIdx.x;
+    if (r < rows && c < cols) {
+      C2 v = tile[threadIdx.x][j];
+      if (conj) v.y = -v.y;
+      dst[(long long)c * rows + r] = v;
+    }
+  }
+}
+
+template <typename C2>
+__global__ void conj_kernel(const C2* __restrict__ src, long long n, C2* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    C2 v = src[i];
+    v.y = -v.y;
+    dst[i] = v;
+  }
+}
+
+template <typename C2>
+__global__ void phys_first_kernel(const C2* __restrict__ src, int a, int b, C2* __restrict__ dst) {
+  const long long n = 2LL * a * b;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long ia = e / (2LL * b);
+    const long long rem = e % (2LL * b);
+    const long long s = rem / b, ib = rem % b;
+    dst[s * a * b + ia * b + ib] = src[e];
+  }
+}
+
+template <typename C2>
+__global__ void identity_kernel(C2* __restrict__ dst, int n) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n, c = e % n;
+    dst[e] = C2{(decltype(C2{}.x))(r == c ? 1 : 0), (decltype(C2{}.x))0};
+  }
+}
+
+template <typename C2>
+__global__ void sum_abs2_kernel(const C2* __restrict__ x, long long n, double* out) {
+  double s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += (double)x[i].x * x[i].x + (double)x[i].y * x[i].y;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) atomicAdd(out, t);
+  }
+}
+
+template <typename C2>
+__global__ void scale_kernel(C2* __restrict__ x, long long n, const double* norm2) {
+  const double nrm = sqrt(*norm2);
+  const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    C2 v = x[i];
+    v.x = (decltype(v.x))(v.x * inv);
+    v.y = (decltype(v.y))(v.y * inv);
+    x[i] = v;
+  }
+}
+
+template <typename C2>
+__global__ void to_z_kernel(const C2* __restrict__ x, long long n, double2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = double2{(double)x[i].x, (double)x[i].y};
+}
+
+}  // namespace
+
+cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void* dst, bool fp64,
+                           cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  if (fp64)
+    transpose_kernel<<<grid, block, 0, st>>>((const double2*)src, rows, cols, conj ? 1 : 0, (double2*)dst);
+  else
+    transpose_kernel<<<grid, block, 0, st>>>((const float2*)src, rows, cols, conj ? 1 : 0, (float2*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_conj(const void* src, long long n, void* dst, bool fp64, cudaStream_t st) {
+  if (fp64) conj_kernel<<<blocks_for(n), 256, 0, st>>>((const double2*)src, n, (double2*)dst);
+  else conj_kernel<<<blocks_for(n), 256, 0, st>>>((const float2*)src, n, (float2*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t permute_phys_first(const void* src, int a, int b, void* dst, bool fp64, cudaStream_t st) {
+  const long long n = 2LL * a * b;
+  if (fp64) phys_first_kernel<<<blocks_for(n), 256, 0, st>>>((const double2*)src, a, b, (double2*)dst);
+  else phys_first_kernel<<<blocks_for(n), 256, 0, st>>>((const float2*)src, a, b, (float2*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(void* dst, int n, bool fp64, cudaStream_t st) {
+  const long long t = (long long)n * n;
+  if (fp64) identity_kernel<<<blocks_for(t), 256, 0, st>>>((double2*)dst, n);
+  else identity_kernel<<<blocks_for(t), 256, 0, st>>>((float2*)dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t set_scalar_one(void* dst, bool fp64, cudaStream_t st) { return set_identity(dst, 1, fp64, st); }
+
+cudaError_t sum_abs2(const void* x, long long n, bool fp64, double* out_dev, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  int b = blocks_for(n);
+  if (b > 1024) b = 1024;
+  if (fp64) sum_abs2_kernel<<<b, 256, 0, st>>>((const double2*)x, n, out_dev);
+  else sum_abs2_kernel<<<b, 256, 0, st>>>((const float2*)x, n, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_inplace(void* x, long long n, const double* norm2_dev, bool fp64, cudaStream_t st) {
+  if (fp64) scale_kernel<<<blocks_for(n), 256, 0, st>>>((double2*)x, n, norm2_dev);
+  else scale_kernel<<<blocks_for(n), 256, 0, st>>>((float2*)x, n, norm2_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t to_complex128(const void* src, long long n, bool fp64, double2* dst, cudaStream_t st) {
+  if (fp64) to_z_kernel<<<blocks_for(n), 256, 0, st>>>((const double2*)src, n, dst);
+  else to_z_kernel<<<blocks_for(n), 256, 0, st>>>((const float2*)src, n, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace dmrgc

@@ -1,0 +1,325 @@
+// Truncated complex SVD by one-sided (Hestenes) Jacobi.
+//
+// theta (or a Gram matrix) is orthogonalised column-pair by column-pair:
+// for a pair (u, v) with alpha = |u|^2, beta = |v|^2, gamma = u^+ v, a unitary
+// 2x2 rotation zeroes gamma.  Pairs follow the round-robin (circle) order, so
+// one round holds n/2 disjoint pairs that run in parallel, one warp per pair;
+// n-1 rounds make a sweep.  All sweeps run in one persistent cooperative
+// kernel: rounds are separated by a grid barrier whose wait is bounded (an
+// exhausted wait sets an error flag and every CTA returns).  Convergence: a
+// sweep whose largest |gamma|/sqrt(alpha beta) is below tol ends the loop.
+//
+// On return the columns of W = G V are mutually orthogonal; their norms are
+// the singular values and W_j / |W_j| the left singular vectors (Eckart-Young
+// truncation then keeps the k largest, Eq. optimization with the bond
+// constraint).  The side computed this way is orthonormal to working
+// precision, which is why callers orthogonalise theta for a left-to-right
+// update and theta^+ for a right-to-left one.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace dmrgc {
+namespace {
+
+struct JacobiCtl {
+  unsigned count;
+  unsigned gen;
+  unsigned off_bits[2];   // float bits of the largest relative off-diagonal of a sweep
+  int err;                // 0 ok, DMRGC_ETIMEOUT, DMRGC_ENOCONV
+  int sweeps;             // sweeps executed
+  int pad[2];
+};
+
+constexpr unsigned long long kSpinLimit = 20000000ull;  // x ~64 ns = ~1.3 s
+
+__device__ __forceinline__ bool grid_barrier(JacobiCtl* c, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &c->gen;
+    volatile int* verr = &c->err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&c->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&c->count, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (*vgen == g) {
+        __nanosleep(64);
+        if (*verr != 0) break;
+        if (++it > kSpinLimit) {
+          atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&c->err) == 0;
+}
+
+__device__ __forceinline__ void round_robin_pair(int r, int p, int np, int& a, int& b) {
+  // circle method: player 0 fixed, players 1..np-1 rotate
+  auto idx = [&](int x) { return (x + r) % (np - 1) + 1; };
+  if (p == 0) { a = 0; b = idx(0); }
+  else { a = idx(p); b = idx(np - 1 - p); }
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __restrict__ G, int m,
+                                                     int n, int np, R tol, int max_sweeps,
+                                                     JacobiCtl* ctl) {
+  using C2 = typename cplx<R>::T;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned nb = gridDim.x;
+  const R tiny = (sizeof(R) == 8) ? (R)1e-280 : (R)1e-30;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int p = warp; p < np / 2; p += nwarps) {
+        int a, b;
+        round_robin_pair(r, p, np, a, b);
+        if (a >= n || b >= n) continue;
+        C2* u = G + (long long)a * m;
+        C2* v = G + (long long)b * m;
+        R al = 0, be = 0, gr = 0, gi = 0;
+        for (int i = lane; i < m; i += 32) {
+          const C2 x = u[i], y = v[i];
+          al += x.x * x.x + x.y * x.y;
+          be += y.x * y.x + y.y * y.y;
+          gr += x.x * y.x + x.y * y.y;   // conj(x) * y
+          gi += x.x * y.y - x.y * y.x;
+        }
+        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        const R gabs = sqrt(gr * gr + gi * gi);
+        if (al <= tiny || be <= tiny || gabs <= tiny) continue;
+        const R rel = gabs / sqrt(al * be);
+        if (!(rel > tol)) continue;
+        local_off = fmaxf(local_off, (float)rel);
+        // phase e^{-i phi} of gamma, real rotation on (u, e^{-i phi} v)
+        const R er = gr / gabs, ei = -gi / gabs;
+        const R zeta = (al - be) / (2 * gabs);
+        const R sg = zeta >= 0 ? R(1) : R(-1);
+        const R t = -sg / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        const R c = R(1) / sqrt(R(1) + t * t);
+        const R s = c * t;
+        // u' = c u - s e^{-i phi} v ;  v' = s u + c e^{-i phi} v
+        for (int i = lane; i < m; i += 32) {
+          const C2 x = u[i], y = v[i];
+          const C2 ye{y.x * er - y.y * ei, y.x * ei + y.y * er};
+          u[i] = C2{c * x.x - s * ye.x, c * x.y - s * ye.y};
+          v[i] = C2{s * x.x + c * ye.x, s * x.y + c * ye.y};
+        }
+      }
+      if (lane == 0 && local_off > 0.f)
+        atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(local_off));
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) return;
+      if (r == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > (float)tol)) { ++sweep; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > (float)tol && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
+// ---- column norms, sort, truncation rank
+
+template <typename R>
+__global__ void col_norms_kernel(const typename cplx<R>::T* __restrict__ W, int m, int n,
+                                 double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (col >= n) return;
+  const auto* w = W + (long long)col * m;
+  double s = 0;
+  for (int i = lane; i < m; i += 32) s += (double)w[i].x * w[i].x + (double)w[i].y * w[i].y;
+  s = warp_sum(s);
+  if (lane == 0) out[col] = s;
+}
+
+// single CTA: bitonic sort of (value, index) descending over the next power of two
+__global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const double* nrm2,
+                                  int n, int chi, double rel_cut, int squared) {
+  extern __shared__ unsigned char smem[];
+  int np = 1;
+  while (np < n) np <<= 1;
+  double* v = reinterpret_cast<double*>(smem);
+  int* ix = reinterpret_cast<int*>(v + np);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    if (i < n) {
+      const double q = nrm2[i];   // |W_i|^2
+      // singular value of theta: |W_i|; of a Gram matrix: |W_i| = s^2
+      v[i] = squared ? sqrt(sqrt(q)) : sqrt(q);
+      ix[i] = i;
+    } else {
+      v[i] = -1.0;
+      ix[i] = -1;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= np; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool desc = (i & k) == 0;
+          const bool swap = desc ? (v[i] < v[l] || (v[i] == v[l] && ix[i] > ix[l]))
+                                 : (v[i] > v[l] || (v[i] == v[l] && ix[i] < ix[l]));
+          if (swap) {
+            double tv = v[i]; v[i] = v[l]; v[l] = tv;
+            int ti = ix[i]; ix[i] = ix[l]; ix[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { s[i] = v[i]; perm[i] = ix[i]; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double s1 = v[0];
+    int k = 0;
+    double f = 0, tot = 0;
+    for (int i = 0; i < n; ++i) tot += v[i] * v[i];
+    for (int i = 0; i < n && k < chi; ++i) {
+      if (v[i] > rel_cut * s1) { f += v[i] * v[i]; ++k; } else break;
+    }
+    res->status = 0;
+    if (!(s1 > 0.0) || !isfinite(s1)) { res->status = (int)DMRGC_ENUMERIC; k = k > 0 ? k : 1; }
+    if (k < 1) k = 1;
+    res->k = k;
+    res->n = n;
+    res->f = f;
+    res->norm2 = tot;
+  }
+}
+
+template <typename R>
+__global__ void gather_kernel(const typename cplx<R>::T* __restrict__ W, int m, int k,
+                              const double* __restrict__ s, const int* __restrict__ perm, int squared,
+                              int mode, typename cplx<R>::T* __restrict__ out) {
+  const long long total = (long long)m * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int row, j;
+    if (mode == 0) { row = (int)(e / k); j = (int)(e % k); }
+    else { j = (int)(e / m); row = (int)(e % m); }
+    const double sj = s[j];
+    const double scale = squared ? sj * sj : sj;
+    const R inv = scale > 0 ? (R)(1.0 / scale) : (R)0;
+    auto w = W[(long long)perm[j] * m + row];
+    if (mode == 2) w.y = -w.y;
+    w.x *= inv;
+    w.y *= inv;
+    if (mode == 0) out[(long long)row * k + j] = w;
+    else out[(long long)j * m + row] = w;
+  }
+}
+
+}  // namespace
+
+size_t jacobi_ctl_bytes() { return sizeof(JacobiCtl); }
+
+cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
+                                 void* ctl, cudaStream_t st, int* launches) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(JacobiCtl), st);
+  if (e != cudaSuccess) return e;
+  if (n < 2 || m < 1) return cudaSuccess;
+  const int np = (n + 1) & ~1;
+  const int threads = 128;
+  const int pairs = np / 2;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* fn = fp64 ? (void*)jacobi_kernel<double> : (void*)jacobi_kernel<float>;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+  if (e != cudaSuccess) return e;
+  int blocks = (pairs + threads / 32 - 1) / (threads / 32);
+  const int cap = sms * (per_sm < 2 ? per_sm : 2);
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  JacobiCtl* c = reinterpret_cast<JacobiCtl*>(ctl);
+  if (fp64) {
+    double tl = tol;
+    double2* g = reinterpret_cast<double2*>(G);
+    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, &c};
+    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
+  } else {
+    float tl = (float)tol;
+    float2* g = reinterpret_cast<float2*>(G);
+    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, &c};
+    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
+  }
+  if (launches) *launches += 1;
+  return e;
+}
+
+size_t trunc_bytes(int n) {
+  return sizeof(TruncResult) + sizeof(double) * (size_t)n + sizeof(int) * (size_t)n + 64;
+}
+
+cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, double rel_cut,
+                             bool squared, void* res, cudaStream_t st) {
+  TruncResult* r = reinterpret_cast<TruncResult*>(res);
+  double* s = reinterpret_cast<double*>(r + 1);
+  int* perm = reinterpret_cast<int*>(s + n);
+  // column norms go to the s array first (then sorted in place via shared memory)
+  const int threads = 256;
+  const int blocks = (n * 32 + threads - 1) / threads;
+  if (fp64)
+    col_norms_kernel<double><<<blocks, threads, 0, st>>>(reinterpret_cast<const double2*>(W), m, n, s);
+  else
+    col_norms_kernel<float><<<blocks, threads, 0, st>>>(reinterpret_cast<const float2*>(W), m, n, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int np = 1;
+  while (np < n) np <<= 1;
+  const size_t sm = (size_t)np * (sizeof(double) + sizeof(int));
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(sort_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  sort_trunc_kernel<<<1, 1024, sm, st>>>(r, s, perm, s, n, chi, rel_cut, squared ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void* res,
+                           bool squared, int mode, void* out, bool fp64, cudaStream_t st) {
+  const TruncResult* r = reinterpret_cast<const TruncResult*>(res);
+  const double* s = reinterpret_cast<const double*>(r + 1);
+  const int* perm = reinterpret_cast<const int*>(s + n_total);
+  const long long total = (long long)m * k;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  if (fp64)
+    gather_kernel<double><<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(W), m, k, s, perm,
+                                                  squared ? 1 : 0, mode,
+                                                  reinterpret_cast<double2*>(out));
+  else
+    gather_kernel<float><<<blocks, 256, 0, st>>>(reinterpret_cast<const float2*>(W), m, k, s, perm,
+                                                 squared ? 1 : 0, mode,
+                                                 reinterpret_cast<float2*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace dmrgc

@@ -1,0 +1,216 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 mode agrees with the complex128 oracle to 1e-10 on
+amplitudes and partial fidelities (the requirement); the FP32 mode (complex64
+storage, FP32 arithmetic) to 1e-4 relative on F_tilde and 1e-4 absolute on
+normalised amplitudes of a 12-qubit state (|amp| ~ 2^-6, FP32 rounding
+~1e-7 per operation accumulated over ~10^4 operations).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dmrg as od
+from oracle import statevector as sv
+from synthetic import circuits as sc
+from tests.helpers import all_bitstrings, gpu_run, min_gap, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _fp64():
+    from paper_2207_05612_gb300 import DMRGC_FP64
+    return DMRGC_FP64
+
+
+def test_config1_exact_fp64():
+    """12 qubits, 3x4 grid, 8 cycles, chi = 64 = 2^{N/2}: exact (T1)."""
+    circ = sc.random_circuit(3, 4, 8, seed=0)
+    ctx, per = gpu_run(circ, 64, precision=_fp64())
+    exact = sv.run(12, circ.layers)[-1]
+    bits = all_bitstrings(12)
+    amp = ctx.amplitude(bits)
+    want = sv.amplitudes(exact, bits)
+    assert np.abs(amp - want).max() < 1e-10
+    lf, fd = ctx.fidelity()
+    assert abs(lf) < 1e-12
+    for p in per:
+        assert abs(p["f_delta"] - 1) < 1e-12
+        assert len(p["hist"]) == 2 * 11
+
+
+@pytest.mark.parametrize("rows,cols,chi,seed", [(3, 4, 8, 1), (3, 4, 12, 2), (2, 6, 6, 3), (3, 5, 20, 4)])
+def test_truncated_parity_fp64(rows, cols, chi, seed):
+    """Truncated regime: every partial fidelity of every layer, F_tilde and the
+    amplitudes agree with the oracle (same algorithm, same truncation)."""
+    circ = sc.random_circuit(rows, cols, 8, seed=seed)
+    order, states, results, log_ft = oracle_run(circ, chi)
+    gap = min_gap(results, chi)
+    ctx, per = gpu_run(circ, chi, precision=_fp64())
+    for p, r in zip(per, results):
+        assert len(p["hist"]) == len(r.f)
+        assert np.abs(np.array(p["hist"]) - np.array(r.f)).max() < 1e-10
+    lf, _ = ctx.fidelity()
+    assert abs(lf - log_ft) < 1e-10
+    n = rows * cols
+    bits = sc.random_bitstrings(n, 200, seed=seed)
+    want = np.array([od.amplitude(states[-1], order, b) for b in bits])
+    got = ctx.amplitude(bits)
+    if gap > 1e-8:
+        assert np.abs(got - want).max() < 1e-10, f"gap {gap}"
+    else:   # degenerate truncation: several optima, compare the norm only
+        assert abs(np.linalg.norm(got) - np.linalg.norm(want)) < 1e-6
+
+
+def test_mps_canonical_form_fp64():
+    circ = sc.random_circuit(3, 4, 6, seed=5)
+    ctx, _ = gpu_run(circ, 10, precision=_fp64())
+    mps, centre = ctx.get_mps()
+    assert centre == 6
+    for i, a in enumerate(mps):
+        al, _, ar = a.shape
+        if i < centre:
+            m = a.reshape(al * 2, ar)
+            assert np.allclose(m.conj().T @ m, np.eye(ar), atol=1e-12)
+        elif i > centre:
+            m = a.reshape(al, 2 * ar)
+            assert np.allclose(m @ m.conj().T, np.eye(al), atol=1e-12)
+    assert abs(np.linalg.norm(mps[centre]) - 1) < 1e-12
+
+
+def test_f_monotone_and_overlap_identity_fp64():
+    """Sec. IV.B.1 (f never decreases) and Eq. (fa-sup) on the GPU state."""
+    circ = sc.random_circuit(2, 5, 6, seed=7)
+    from paper_2207_05612_gb300 import Context
+    ctx = Context(2, 5, 6, precision=_fp64())
+    order = [0, 5, 6, 1, 2, 7, 8, 3, 4, 9]
+    prev = sv.zero_state(10)
+    for layer in circ.layers:
+        ctx.apply_layer(layer)
+        ctx.sweep(2)
+        h = np.array(ctx.history())
+        assert np.all(np.diff(h) >= -1e-13)
+        mps, _ = ctx.get_mps()
+        new = od.mps_dense(mps, order)
+        target = sv.apply_layer(prev, layer)
+        ov = np.vdot(new.reshape(-1), target.reshape(-1))
+        assert abs(abs(ov) ** 2 - h[-1]) < 1e-11
+        prev = new
+
+
+def test_qaoa_exact_fp64():
+    circ, g, b, edges = sc.qaoa_circuit(3, 4, 2, seed=3)
+    ctx, per = gpu_run(circ, 64, precision=_fp64())
+    exact = sv.run(12, circ.layers)[-1]
+    bits = all_bitstrings(12)
+    assert np.abs(ctx.amplitude(bits) - sv.amplitudes(exact, bits)).max() < 1e-10
+
+
+def test_sampler_matches_oracle_fp64():
+    """Same SplitMix64 stream on both sides: identical bit strings."""
+    circ = sc.random_circuit(2, 4, 4, seed=2)
+    order, states, results, _ = oracle_run(circ, 16)
+    ctx, _ = gpu_run(circ, 16, precision=_fp64())
+    got = ctx.sample(400, seed=99)
+    want = od.sample(states[-1], order, 4, 400, seed=99)
+    assert np.array_equal(got, want)
+
+
+def test_sampler_distribution_fp64():
+    from scipy.stats import chisquare
+    circ = sc.random_circuit(2, 4, 4, seed=3)
+    ctx, _ = gpu_run(circ, 16, precision=_fp64())
+    exact = sv.run(8, circ.layers)[-1]
+    p = (np.abs(exact) ** 2).reshape(-1)
+    count = 20000
+    smp = ctx.sample(count, seed=5)
+    idx = np.zeros(count, dtype=int)
+    for q in range(8):
+        idx = idx * 2 + smp[:, q].astype(int)
+    obs = np.bincount(idx, minlength=256)
+    keep = p * count > 5
+    stat = chisquare(obs[keep], p[keep] * count * obs[keep].sum() / (p[keep] * count).sum())
+    assert stat.pvalue > 1e-4
+
+
+def test_fp32_mode_against_oracle():
+    from paper_2207_05612_gb300 import DMRGC_FP32
+    circ = sc.random_circuit(3, 4, 8, seed=1)
+    order, states, results, log_ft = oracle_run(circ, 16)
+    ctx, per = gpu_run(circ, 16, precision=DMRGC_FP32)
+    lf, _ = ctx.fidelity()
+    assert abs(lf - log_ft) <= 1e-4 * abs(log_ft) + 1e-6
+    bits = sc.random_bitstrings(12, 200, seed=3)
+    want = np.array([od.amplitude(states[-1], order, b) for b in bits])
+    assert np.abs(ctx.amplitude(bits) - want).max() < 1e-4
+
+
+def test_fp32_exact_regime():
+    from paper_2207_05612_gb300 import DMRGC_FP32
+    circ = sc.random_circuit(3, 4, 8, seed=0)
+    ctx, per = gpu_run(circ, 64, precision=DMRGC_FP32)
+    exact = sv.run(12, circ.layers)[-1]
+    bits = all_bitstrings(12)
+    assert np.abs(ctx.amplitude(bits) - sv.amplitudes(exact, bits)).max() < 1e-5
+    lf, _ = ctx.fidelity()
+    assert abs(lf) < 1e-5
+
+
+def test_ragged_sizes_fp64():
+    """Bond dimensions that are not multiples of the 64-wide GEMM tiles and a
+    24-qubit grid whose environments span several tiles."""
+    circ = sc.random_circuit(4, 6, 4, seed=8)
+    order, states, results, log_ft = oracle_run(circ, 37)
+    ctx, per = gpu_run(circ, 37, precision=_fp64())
+    for p, r in zip(per, results):
+        assert np.abs(np.array(p["hist"]) - np.array(r.f)).max() < 1e-10
+    gap = min_gap(results, 37)
+    bits = sc.random_bitstrings(24, 100, seed=1)
+    want = np.array([od.amplitude(states[-1], order, b) for b in bits])
+    got = ctx.amplitude(bits)
+    scale = np.abs(want).max()
+    if gap > 1e-8:
+        assert np.abs(got - want).max() < 1e-10 * max(1.0, scale * 1e4)
+
+
+# ----------------------------------------------------------------- edge cases
+
+
+def test_edge_single_qubit_and_pair():
+    for rows, cols in [(1, 1), (1, 2)]:
+        circ = sc.random_circuit(rows, cols, 4, seed=1)
+        n = rows * cols
+        ctx, per = gpu_run(circ, 4, precision=_fp64())
+        exact = sv.run(n, circ.layers)[-1]
+        bits = all_bitstrings(n)
+        assert np.abs(ctx.amplitude(bits) - sv.amplitudes(exact, bits)).max() < 1e-12
+
+
+def test_edge_chi_one_and_empty_layer():
+    circ = sc.random_circuit(2, 3, 2, seed=4)
+    order, states, results, log_ft = oracle_run(circ, 1)
+    ctx, per = gpu_run(circ, 1, precision=_fp64())
+    lf, _ = ctx.fidelity()
+    assert abs(lf - log_ft) < 1e-10
+    from paper_2207_05612_gb300 import Context
+    c2 = Context(2, 3, 8, precision=_fp64())
+    c2.apply_layer([])          # identity layer
+    c2.sweep(2)
+    bits = all_bitstrings(6)
+    amp = c2.amplitude(bits)
+    assert abs(amp[0] - 1) < 1e-14 and np.abs(amp[1:]).max() < 1e-14
+
+
+def test_edge_errors():
+    from paper_2207_05612_gb300 import Context, DmrgcError
+    ctx = Context(2, 2, 4, precision=_fp64())
+    with pytest.raises(DmrgcError) as e:
+        ctx.sweep(2)
+    assert e.value.status == 7          # ESTATE
+    with pytest.raises(DmrgcError) as e:
+        ctx.apply_layer([(0, 9, np.eye(4))])
+    assert e.value.status == 1          # EINVAL
+    with pytest.raises(DmrgcError) as e:
+        ctx.amplitude(np.full((1, 4), 2, dtype=np.uint8))
+    assert e.value.status == 1
