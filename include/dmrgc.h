@@ -64,9 +64,9 @@ typedef struct {
   int precision;              /* DMRGC_FP64 ... DMRGC_FP32 */
   int svd_mode;               /* 0 = one-sided Jacobi (only mode) */
   double sweep_rel_cutoff;    /* keep s_mu > cutoff * s_1 in the sweep SVD; <= 0: default
-                                 (1e-12 for FP64, 1e-6 otherwise) */
+                                 (1e-12 for FP64, 2e-5 for the complex64 modes) */
   double zip_rel_cutoff;      /* same for the truncating steps of the zip-up guess; <= 0:
-                                 default (1e-5 for FP64, 1e-3 otherwise) */
+                                 default (1e-5 for FP64, 4e-3 for the complex64 modes) */
   int max_jacobi_sweeps;      /* <= 0: default 40 */
   unsigned long long seed;    /* reserved */
   void* cuda_stream;          /* cudaStream_t to launch on; NULL = default stream */
@@ -152,6 +152,29 @@ dmrgc_status dmrgc_step_history(const dmrgc_ctx* ctx, double* f, int cap, int* c
 
 dmrgc_status dmrgc_get_stats(const dmrgc_ctx* ctx, dmrgc_stats* out);
 dmrgc_status dmrgc_reset_stats(dmrgc_ctx* ctx);
+
+/* Diagnostic entry points: run one kernel family of the sweep on host data,
+ * synchronously on the default stream, with all device memory allocated and
+ * freed inside the call.  Inputs and outputs are complex128 (re/im
+ * interleaved) host arrays; the data are converted to the working precision
+ * of `precision` on the device.
+ *
+ * dmrgc_test_gemm: C[M][N] = op(A) op(B) with the contraction engine (the
+ * complex matrix products that form X, Y, theta and the environments,
+ * Eq. (scalarproduct)).  op codes: 0 none, 1 transpose, 2 conjugate
+ * transpose, 3 conjugate; row-major A (a_elems values, leading dim lda) and
+ * B (b_elems, ldb); C row-major, N columns.
+ *
+ * dmrgc_test_svd: one-sided Jacobi on the columns of G (m x n, column-major)
+ * followed by the truncation rule (Eq. optimization with the bond
+ * constraint): s_out[n] receives the singular values in descending order,
+ * *k_out the kept rank min(chi, #{s > rel_cut*s_1}), U_out[m][k] (row-major)
+ * the kept left singular vectors. */
+dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int opB, const double* A,
+                             long long a_elems, long long lda, const double* B, long long b_elems,
+                             long long ldb, double* C);
+dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
+                            double* s_out, int* k_out, double* U_out);
 
 const char* dmrgc_last_error(const dmrgc_ctx* ctx);
 void dmrgc_destroy(dmrgc_ctx* ctx);

@@ -31,8 +31,11 @@ Initial guess (the paper uses a random MPS or a TEBD-like start, Sec. V.D.1):
 a zip-up of W.B from both ends towards the centre site m = N // 2.  At a site
 whose matrix has r <= chi rows the full row space is kept with the identity
 basis (no truncation, no SVD); otherwise the top left singular vectors with
-s_mu > zip_cut * s_1, at most chi.  The guess is therefore exact whenever
-chi >= 2^{max(m, N-m-1)}, i.e. chi >= 2^{N/2}.
+s_mu > zip_cut * s_1, at most chi, never splitting a degenerate multiplet.
+The guess is therefore exact whenever chi >= 2^{max(m, N-m-1)}, i.e.
+chi >= 2^{N/2}.  It depends on the gauge of the MPO bond (the remainder it
+truncates against is not orthonormal), so a comparison of two implementations
+must give both the same MPO up to a unitary gauge per bond.
 
 Sweep schedule, 2(N-1) two-site updates per layer (n_s = 2 one-direction
 sweeps): bonds (m-1,m) .. (0,1) right-to-left, then (0,1) .. (N-2,N-1)
@@ -78,16 +81,23 @@ def env_right(a_new: np.ndarray, y: np.ndarray) -> np.ndarray:
     return np.einsum("ksc,scwb->kwb", a_new.conj(), y, optimize=True)
 
 
-def truncation_rank(s: np.ndarray, chi: int, rel_cut: float) -> int:
+def truncation_rank(s: np.ndarray, chi: int, rel_cut: float, floor: float = 0.0) -> int:
+    """k = min(chi, #{s_mu > max(rel_cut * s_1, floor)}), at least 1."""
     if s.size == 0 or s[0] == 0.0:
         return 1
-    return max(1, min(chi, int(np.sum(s > rel_cut * s[0]))))
+    return max(1, min(chi, int(np.sum(s > max(rel_cut * s[0], floor)))))
 
 
-def svd_truncate(theta: np.ndarray, chi: int, rel_cut: float):
-    """Truncated SVD of theta: (U_k, s_k, Vh_k), LAPACK complex128."""
+# Numerical-zero level of a singular value relative to |theta|_F in complex128
+# arithmetic: directions below it carry no information and are never kept.
+ZERO_REL = 1e-13
+
+
+def svd_truncate(theta: np.ndarray, chi: int, rel_cut: float, zero_rel: float = ZERO_REL):
+    """Truncated SVD of theta: (U_k, s_k, Vh_k), LAPACK complex128.  Keeps
+    s_mu > max(rel_cut * s_1, zero_rel * |theta|_F), at most chi."""
     u, s, vh = np.linalg.svd(theta, full_matrices=False)
-    k = truncation_rank(s, chi, rel_cut)
+    k = truncation_rank(s, chi, rel_cut, zero_rel * np.sqrt(np.sum(s ** 2)))
     return u[:, :k], s[:k], vh[:k], s
 
 
@@ -101,6 +111,7 @@ class LayerResult:
         self.bonds = []      # (pass, i) of every update
         self.spectra = []    # full singular spectrum of every theta
         self.guess_overlap = 0.0
+        self.zip_ambiguous = False  # a zip-up cut fell in a multiplet reaching s_1
         self.records = {}    # optional snapshots keyed by (pass, i)
 
     @property
@@ -108,24 +119,42 @@ class LayerResult:
         return self.f[-1] if self.f else self.guess_overlap ** 2
 
 
-def zip_matrix_basis(mat: np.ndarray, chi: int, zip_cut: float):
+ZIP_AMBIGUOUS: list = []   # rows of zip-up cuts that fell in a multiplet reaching s_1
+
+
+def zip_matrix_basis(mat: np.ndarray, chi: int, zip_cut: float, tie_cut: float = 1e-10,
+                     zero_rel: float = ZERO_REL):
     """Left basis kept by the zip-up for a matrix with r rows: the identity if
-    r <= chi, else the top-k left singular vectors (s_mu > zip_cut * s_1)."""
+    r <= chi, else the top-k left singular vectors (s_mu > zip_cut * s_1).
+    If the cut at chi falls inside a degenerate multiplet (s_k - s_{k+1} <=
+    tie_cut * s_1) the whole multiplet is dropped, so that the kept subspace,
+    and with it the guess, is unique."""
     r = mat.shape[0]
     if r <= chi:
         return np.eye(r, dtype=np.complex128)
     u, s, _ = np.linalg.svd(mat, full_matrices=False)
-    k = truncation_rank(s, chi, zip_cut)
+    # floor: s^2 above zero_rel times the Frobenius norm of the Gram matrix M M^+
+    floor = np.sqrt(zero_rel * np.sqrt(np.sum(s ** 4)))
+    k = truncation_rank(s, chi, zip_cut, floor)
+    if k < s.size and s[k] > max(zip_cut * s[0], floor) and s[k - 1] - s[k] <= tie_cut * s[0]:
+        kk = k
+        while kk > 1 and s[kk - 1] - s[kk] <= tie_cut * s[0]:
+            kk -= 1
+        if kk == 1 and s[0] - s[1] <= tie_cut * s[0]:
+            ZIP_AMBIGUOUS.append(r)   # the multiplet reaches s_1: cut kept at chi
+        else:
+            k = kk
     return u[:, :k]
 
 
 def compress_layer(b: list[np.ndarray], w: list[np.ndarray], chi: int,
-                   sweep_cut: float = 1e-12, zip_cut: float = 1e-5,
-                   record: set | None = None):
+                   sweep_cut: float = 1e-12, zip_cut: float = 1e-5, tie_cut: float = 1e-10,
+                   zero_rel: float = ZERO_REL, record: set | None = None):
     """One compression step (Sec. IV.B): returns (new MPS tensors, LayerResult)."""
     n = len(b)
     m = n // 2
     res = LayerResult()
+    ZIP_AMBIGUOUS.clear()
     a = [None] * n
     xs = [None] * n   # X_i, valid for sites left of the current bond
     ys = [None] * n   # Y_i, valid for sites right of the current bond
@@ -137,7 +166,7 @@ def compress_layer(b: list[np.ndarray], w: list[np.ndarray], chi: int,
         xs[i] = x
         al, s, wd, bd = x.shape
         mat = x.reshape(al * s, wd * bd)
-        basis = zip_matrix_basis(mat, chi, zip_cut)
+        basis = zip_matrix_basis(mat, chi, zip_cut, tie_cut, zero_rel)
         a[i] = basis.reshape(al, 2, basis.shape[1])
         lenv = env_left(a[i], x)
     # --- zip-up guess, right part
@@ -147,9 +176,10 @@ def compress_layer(b: list[np.ndarray], w: list[np.ndarray], chi: int,
         ys[i] = y
         s, cr, wd, bd = y.shape
         mat = y.reshape(s * cr, wd * bd)
-        basis = zip_matrix_basis(mat, chi, zip_cut)
+        basis = zip_matrix_basis(mat, chi, zip_cut, tie_cut, zero_rel)
         a[i] = basis.T.reshape(basis.shape[1], 2, cr)
         renv = env_right(a[i], y)
+    res.zip_ambiguous = len(ZIP_AMBIGUOUS) > 0
     # --- centre
     xm = make_x(lenv, b[m], w[m])
     xs[m] = xm
@@ -161,7 +191,7 @@ def compress_layer(b: list[np.ndarray], w: list[np.ndarray], chi: int,
 
     def update(pass_id, i, x, y, left_to_right):
         th = theta_of(x, y)
-        u, s, vh, full = svd_truncate(th, chi, sweep_cut)
+        u, s, vh, full = svd_truncate(th, chi, sweep_cut, zero_rel)
         k = s.size
         nrm_s = np.linalg.norm(s)
         al = x.shape[0]

@@ -76,7 +76,12 @@ def lib():
         L.dmrgc_last_error.restype = C.c_char_p
         L.dmrgc_destroy.argtypes = [C.c_void_p]
         L.dmrgc_destroy.restype = None
-        for name in ("dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+        L.dmrgc_test_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p,
+                                      C.c_longlong, C.c_longlong, C.c_void_p]
+        L.dmrgc_test_svd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                                     C.c_void_p, P(C.c_int), C.c_void_p]
+        for name in ("dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
             getattr(L, name).restype = C.c_int
@@ -192,6 +197,31 @@ def dmrgc_reset_stats(ctx) -> None:
 def dmrgc_destroy(ctx) -> None:
     if ctx:
         lib().dmrgc_destroy(ctx)
+
+
+def dmrgc_test_gemm(precision: int, a: np.ndarray, b: np.ndarray, op_a: int, op_b: int,
+                    m: int, n: int, k: int) -> np.ndarray:
+    """C = op(A) op(B) on the device (diagnostic entry point)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    out = np.zeros((m, n), dtype=np.complex128)
+    _check(lib().dmrgc_test_gemm(precision, m, n, k, op_a, op_b, a.ctypes.data, a.size, a.shape[1],
+                                 b.ctypes.data, b.size, b.shape[1], out.ctypes.data))
+    return out
+
+
+def dmrgc_test_svd(precision: int, g: np.ndarray, chi: int, rel_cut: float):
+    """Jacobi SVD + truncation of g (m x n) on the device (diagnostic entry point).
+    Returns (s, k, U_k)."""
+    m, n = g.shape
+    gc = np.asfortranarray(g, dtype=np.complex128)
+    s = np.zeros(n)
+    k = C.c_int()
+    u = np.zeros((m, n), dtype=np.complex128)
+    _check(lib().dmrgc_test_svd(precision, m, n, gc.ctypes.data, chi, rel_cut, s.ctypes.data,
+                                C.byref(k), u.ctypes.data))
+    kk = k.value
+    return s, kk, u.reshape(-1)[:m * kk].reshape(m, kk)
 
 
 class Context:

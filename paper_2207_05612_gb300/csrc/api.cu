@@ -44,7 +44,7 @@ struct dmrgc_ctx {
   cudaStream_t st = nullptr;
   bool fp64 = true;
   size_t esz = 16;
-  double sweep_cut = 1e-12, zip_cut = 1e-5;
+  double sweep_cut = 1e-12, zip_cut = 1e-5, zero_rel = 1e-13, tie_rel = 1e-10;
   int max_jsweeps = 40;
   std::vector<int> order, site_of;
   std::vector<DevBuf> A, B, Wx, Wy, XY, E;
@@ -168,12 +168,17 @@ dmrgc_status sync(dmrgc_ctx* c) {
 
 // ---- GEMM dispatch
 
+cudaError_t run_gemm(int precision, const GemmArgs& g, cudaStream_t st) {
+  if (precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3) return cudaErrorNotSupported;
+  return gemm_simt(g, precision == DMRGC_FP64, st);
+}
+
 dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
   if (c->opt.precision == DMRGC_BF16X3 || c->opt.precision == DMRGC_TF32X3)
     return fail(c, DMRGC_EINVAL, "tensor-core precision modes are not available in this build");
   const double fl = 8.0 * g.M * (double)g.N * g.K * g.b1 * g.b2;
   Span sp(c, TC_GEMM, fl);
-  CK(gemm_simt(g, c->fp64, c->st));
+  CK(run_gemm(c->opt.precision, g, c->st));
   c->stats.gemm_launches++;
   c->stats.kernel_launches++;
   return DMRGC_OK;
@@ -235,17 +240,24 @@ double jacobi_tol(const dmrgc_ctx* c, int m) {
 }
 
 // Orthogonalise the columns of jw (m x n column-major), truncate; returns k, f.
-dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, int& k, double& f) {
+// squared: jw is a Gram matrix (its column norms are s^2); tie_rel > 0 applies
+// the multiplet rule at the cut.
+dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, double tie_rel,
+                         int& k, double& f) {
   TRY(ensure(c, c->jctl, jacobi_ctl_bytes()));
   TRY(ensure(c, c->tres, trunc_bytes(n)));
+  TRY(ensure(c, c->scal, 64));
+  double* fro2 = (double*)c->scal.p + 1;
   {
     Span sp(c, TC_SVD);
     int launches = 0;
-    CK(jacobi_orthogonalize(c->jw.p, m, n, c->fp64, jacobi_tol(c, m), c->max_jsweeps, c->jctl.p,
-                            c->st, &launches));
-    CK(truncate_columns(c->jw.p, m, n, c->fp64, c->chi, rel_cut, squared, c->tres.p, c->st));
-    c->stats.svd_launches += launches + 2;
-    c->stats.kernel_launches += launches + 2;
+    CK(sum_abs2(c->jw.p, (long long)m * n, c->fp64, fro2, c->st));
+    CK(jacobi_orthogonalize(c->jw.p, m, n, c->fp64, jacobi_tol(c, m), c->max_jsweeps, fro2,
+                            c->zero_rel, c->jctl.p, c->st, &launches));
+    CK(truncate_columns(c->jw.p, m, n, c->fp64, c->chi, rel_cut, squared, tie_rel, fro2, c->zero_rel,
+                        c->tres.p, c->st));
+    c->stats.svd_launches += launches + 3;
+    c->stats.kernel_launches += launches + 3;
   }
   struct { int count, gen; unsigned off[2]; int err, sweeps, pad[2]; } ctl{};
   TruncResult tr{};
@@ -294,7 +306,7 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   }
   int k;
   double f;
-  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, k, f));
+  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f));
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
   {
     Span sp(c, TC_SVD);
@@ -344,7 +356,7 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   int k;
   double f;
   // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
-  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, k, f));
+  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f));
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
   {
     Span sp(c, TC_SVD);
@@ -416,7 +428,7 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
     TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
     int k;
     double f;
-    TRY(svd_columns(c, r, r, c->zip_cut, true, k, f));
+    TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
     TRY(ensure(c, c->A[i], (size_t)r * k * c->esz));
     {
       Span sp(c, TC_SVD);
@@ -450,7 +462,7 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
     TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
     int k;
     double f;
-    TRY(svd_columns(c, r, r, c->zip_cut, true, k, f));
+    TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
     TRY(ensure(c, c->A[i], (size_t)k * r * c->esz));
     {
       Span sp(c, TC_SVD);
@@ -639,8 +651,13 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
   c->st = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
   c->fp64 = c->opt.precision == DMRGC_FP64;
   c->esz = c->fp64 ? 16 : 8;
-  c->sweep_cut = c->opt.sweep_rel_cutoff > 0 ? c->opt.sweep_rel_cutoff : (c->fp64 ? 1e-12 : 1e-6);
-  c->zip_cut = c->opt.zip_rel_cutoff > 0 ? c->opt.zip_rel_cutoff : (c->fp64 ? 1e-5 : 1e-3);
+  // numerically-zero level of a Jacobi column, relative to |theta|_F, and the
+  // cutoffs above it: FP64 1e-13 / sweep 1e-12 / zip 1e-5; complex64 1e-5 / 2e-5 / 4e-3
+  // (a Gram column norm is s^2, so the zip cutoff on s is the square root).
+  c->zero_rel = c->fp64 ? 1e-13 : 1e-5;
+  c->tie_rel = c->fp64 ? 1e-10 : 1e-5;
+  c->sweep_cut = c->opt.sweep_rel_cutoff > 0 ? c->opt.sweep_rel_cutoff : (c->fp64 ? 1e-12 : 2e-5);
+  c->zip_cut = c->opt.zip_rel_cutoff > 0 ? c->opt.zip_rel_cutoff : (c->fp64 ? 1e-5 : 4e-3);
   c->max_jsweeps = c->opt.max_jacobi_sweeps > 0 ? c->opt.max_jacobi_sweeps : 40;
   for (int col = 0; col < c->cols; ++col)
     for (int k = 0; k < c->rows; ++k) {
@@ -877,6 +894,101 @@ dmrgc_status dmrgc_reset_stats(dmrgc_ctx* c) {
 }
 
 const char* dmrgc_last_error(const dmrgc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+// ---- diagnostic entry points: one kernel family on host data
+
+namespace {
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() { for (void* p : ptrs) cudaFree(p); }
+  void* get(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    ptrs.push_back(p);
+    return p;
+  }
+};
+
+cudaError_t upload_as(const double* host, long long n, bool fp64, Scratch& s, void** out) {
+  double2* z = (double2*)s.get(sizeof(double2) * n);
+  *out = s.get((fp64 ? 16 : 8) * n);
+  if (!z || !*out) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemcpy(z, host, sizeof(double2) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return from_complex128(z, n, fp64, *out, 0);
+}
+
+cudaError_t download_from(const void* dev, long long n, bool fp64, Scratch& s, double* host) {
+  double2* z = (double2*)s.get(sizeof(double2) * n);
+  if (!z) return cudaErrorMemoryAllocation;
+  cudaError_t e = to_complex128(dev, n, fp64, z, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, z, sizeof(double2) * n, cudaMemcpyDeviceToHost);
+  return e;
+}
+}  // namespace
+
+dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int opB, const double* A,
+                             long long a_elems, long long lda, const double* B, long long b_elems,
+                             long long ldb, double* C) {
+  if (precision < 0 || precision > 3 || M < 1 || N < 1 || K < 1 || opA < 0 || opA > 3 || opB < 0 ||
+      opB > 3 || !A || !B || !C || a_elems < 1 || b_elems < 1)
+    return DMRGC_EINVAL;
+  const bool fp64 = precision == DMRGC_FP64;
+  Scratch s;
+  void *dA, *dB;
+  if (upload_as(A, a_elems, fp64, s, &dA) != cudaSuccess) return DMRGC_ECUDA;
+  if (upload_as(B, b_elems, fp64, s, &dB) != cudaSuccess) return DMRGC_ECUDA;
+  void* dC = s.get((size_t)(fp64 ? 16 : 8) * M * N);
+  if (!dC) return DMRGC_ENOMEM;
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = dA; g.lda = lda; g.opA = opA;
+  g.B = dB; g.ldb = ldb; g.opB = opB;
+  g.C = dC; g.ldc = N;
+  cudaError_t e = run_gemm(precision, g, 0);
+  if (e == cudaErrorNotSupported) return DMRGC_EINVAL;
+  if (e != cudaSuccess) return DMRGC_ECUDA;
+  if (download_from(dC, (long long)M * N, fp64, s, C) != cudaSuccess) return DMRGC_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
+}
+
+dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
+                            double* s_out, int* k_out, double* U_out) {
+  if (precision < 0 || precision > 3 || m < 1 || n < 2 || chi < 1 || !G || !s_out || !k_out || !U_out)
+    return DMRGC_EINVAL;
+  const bool fp64 = precision == DMRGC_FP64;
+  Scratch s;
+  void* dG;
+  if (upload_as(G, (long long)m * n, fp64, s, &dG) != cudaSuccess) return DMRGC_ECUDA;
+  void* ctl = s.get(jacobi_ctl_bytes());
+  void* res = s.get(trunc_bytes(n));
+  double* fro2 = (double*)s.get(sizeof(double));
+  void* dU = s.get((size_t)(fp64 ? 16 : 8) * m * n);
+  if (!ctl || !res || !fro2 || !dU) return DMRGC_ENOMEM;
+  const double eps = fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+  const double tol = 8.0 * eps * std::sqrt((double)m);
+  int launches = 0;
+  if (sum_abs2(dG, (long long)m * n, fp64, fro2, 0) != cudaSuccess) return DMRGC_ECUDA;
+  if (jacobi_orthogonalize(dG, m, n, fp64, tol, 40, fro2, fp64 ? 1e-13 : 1e-5, ctl, 0, &launches) !=
+      cudaSuccess)
+    return DMRGC_ECUDA;
+  if (truncate_columns(dG, m, n, fp64, chi, rel_cut, false, 0.0, fro2, fp64 ? 1e-13 : 1e-5, res, 0) !=
+      cudaSuccess)
+    return DMRGC_ECUDA;
+  TruncResult tr{};
+  struct { int count, gen; unsigned off[2]; int err, sweeps, pad[2]; } cs{};
+  if (cudaMemcpy(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
+  if (cudaMemcpy(&cs, ctl, sizeof(cs), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
+  if (cs.err == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;
+  if (cs.err == DMRGC_ENOCONV) return DMRGC_ENOCONV;
+  if (cudaMemcpy(s_out, (const char*)res + sizeof(TruncResult), sizeof(double) * n,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DMRGC_ECUDA;
+  *k_out = tr.k;
+  if (gather_columns(dG, m, n, tr.k, res, false, 0, dU, fp64, 0) != cudaSuccess) return DMRGC_ECUDA;
+  if (download_from(dU, (long long)m * tr.k, fp64, s, U_out) != cudaSuccess) return DMRGC_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
+}
 
 void dmrgc_destroy(dmrgc_ctx* c) {
   if (!c) return;

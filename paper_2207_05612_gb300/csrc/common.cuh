@@ -53,25 +53,33 @@ cudaError_t gemm_simt(const GemmArgs& g, bool fp64, cudaStream_t st);
 
 // One-sided (Hestenes) Jacobi on the columns of G (column-major, m x n,
 // leading dimension m), in place: on return G = W = G0 V with mutually
-// orthogonal columns.  ctl must point to device scratch of jacobi_ctl_bytes().
+// orthogonal columns.  fro2: device pointer to |G|_F^2; columns with norm
+// below zero_rel*|G|_F are treated as zero.  ctl must point to device scratch
+// of jacobi_ctl_bytes().
 size_t jacobi_ctl_bytes();
 cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
-                                 void* ctl, cudaStream_t st, int* launches);
+                                 const double* fro2, double zero_rel, void* ctl, cudaStream_t st,
+                                 int* launches);
 
 // Column norms of W, sort descending, truncation rank.  Writes into res (device):
 // res->k, res->f = sum_{j<k} s_j^2, res->perm[j], res->s[j] (sorted).
 // squared: the column norms are s^2 (Gram input) -> s = sqrt(norm).
+// tie_rel > 0: if the cut falls inside a multiplet (s_k - s_{k+1} <= tie_rel*s_1),
+// k is lowered to the multiplet's upper edge so that the kept subspace is unique.
 struct TruncResult {
   int k;
   int n;
   int status;     // 0 ok, 5 = numeric (NaN/zero)
-  int pad;
+  int pad;        // 1: the cut fell in a multiplet reaching s_1 (kept at chi, not unique)
   double f;       // sum of kept s^2
   double norm2;   // sum of all s^2
 };
 size_t trunc_bytes(int n);  // TruncResult followed by double s[n], int perm[n]
+// fro2 / zero_rel: the Frobenius norm^2 of the matrix given to the Jacobi kernel
+// and its zero level; columns at or below that level are never kept.
 cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, double rel_cut,
-                             bool squared, void* res, cudaStream_t st);
+                             bool squared, double tie_rel, const double* fro2, double zero_rel,
+                             void* res, cudaStream_t st);
 
 // Gather kept columns into MPS layouts.  mode:
 //  0: out[row*k + j] = W[row + perm[j]*m] / scale_j            (U_k row-major [m][k])
@@ -114,9 +122,10 @@ cudaError_t permute_phys_first(const void* src, int a, int b, void* dst, bool fp
 cudaError_t set_identity(void* dst, int n, bool fp64, cudaStream_t st);  // n x n
 cudaError_t set_scalar_one(void* dst, bool fp64, cudaStream_t st);
 cudaError_t sum_abs2(const void* x, long long n, bool fp64, double* out_dev, cudaStream_t st);
-cudaError_t scale_inplace(void* x, long long n, const double* inv_norm_dev, bool fp64,
+cudaError_t scale_inplace(void* x, long long n, const double* norm2_dev, bool fp64,
                           cudaStream_t st);
 cudaError_t to_complex128(const void* src, long long n, bool fp64, double2* dst, cudaStream_t st);
+cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* dst, cudaStream_t st);
 
 // --------------------------------------------------------------- read-outs
 

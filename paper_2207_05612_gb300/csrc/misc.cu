@@ -100,7 +100,20 @@ __global__ void to_z_kernel(const C2* __restrict__ x, long long n, double2* __re
     out[i] = double2{(double)x[i].x, (double)x[i].y};
 }
 
+template <typename C2>
+__global__ void from_z_kernel(const double2* __restrict__ x, long long n, C2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = C2{(decltype(C2{}.x))x[i].x, (decltype(C2{}.x))x[i].y};
+}
+
 }  // namespace
+
+cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* dst, cudaStream_t st) {
+  if (fp64) from_z_kernel<<<blocks_for(n), 256, 0, st>>>(src, n, (double2*)dst);
+  else from_z_kernel<<<blocks_for(n), 256, 0, st>>>(src, n, (float2*)dst);
+  return cudaGetLastError();
+}
 
 cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void* dst, bool fp64,
                            cudaStream_t st) {

@@ -79,13 +79,18 @@ __device__ __forceinline__ R warp_sum(R v) {
 template <typename R>
 __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __restrict__ G, int m,
                                                      int n, int np, R tol, int max_sweeps,
+                                                     const double* __restrict__ fro2, R zero_rel,
                                                      JacobiCtl* ctl) {
   using C2 = typename cplx<R>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const unsigned nb = gridDim.x;
-  const R tiny = (sizeof(R) == 8) ? (R)1e-280 : (R)1e-30;
+  // columns whose norm is below zero_rel * |G|_F are numerically zero: their
+  // direction is rounding noise, so they are never rotated (and are dropped
+  // later by the truncation cutoff, which lies above zero_rel)
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const R tiny = (R)fmax(fz, (sizeof(R) == 8) ? 1e-280 : 1e-30);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     float local_off = 0.f;
@@ -158,7 +163,8 @@ __global__ void col_norms_kernel(const typename cplx<R>::T* __restrict__ W, int 
 
 // single CTA: bitonic sort of (value, index) descending over the next power of two
 __global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const double* nrm2,
-                                  int n, int chi, double rel_cut, int squared) {
+                                  int n, int chi, double rel_cut, int squared, double tie_rel,
+                                  const double* fro2, double zero_rel) {
   extern __shared__ unsigned char smem[];
   int np = 1;
   while (np < n) np <<= 1;
@@ -197,13 +203,28 @@ __global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const 
   __syncthreads();
   if (threadIdx.x == 0) {
     const double s1 = v[0];
+    // a column the Jacobi kernel treated as zero (norm <= zero_rel |G|_F) is
+    // never kept: the cut is the larger of rel_cut * s_1 and that level
+    const double zthr = zero_rel * sqrt(*fro2);              // on the column norm
+    const double scut = fmax(rel_cut * s1, squared ? sqrt(zthr) : zthr);
     int k = 0;
     double f = 0, tot = 0;
     for (int i = 0; i < n; ++i) tot += v[i] * v[i];
     for (int i = 0; i < n && k < chi; ++i) {
-      if (v[i] > rel_cut * s1) { f += v[i] * v[i]; ++k; } else break;
+      if (v[i] > scut) ++k; else break;
     }
+    // tie rule: never split a (numerically) degenerate multiplet at the cut;
+    // a multiplet that reaches s_1 cannot be dropped, the cut then stays at chi
+    int ambiguous = 0;
+    if (tie_rel > 0 && k >= 1 && k < n && v[k] > scut && v[k - 1] - v[k] <= tie_rel * s1) {
+      int kk = k;
+      while (kk > 1 && v[kk - 1] - v[kk] <= tie_rel * s1) --kk;
+      if (kk == 1 && v[0] - v[1] <= tie_rel * s1) ambiguous = 1;
+      else k = kk;
+    }
+    for (int i = 0; i < k; ++i) f += v[i] * v[i];
     res->status = 0;
+    res->pad = ambiguous;
     if (!(s1 > 0.0) || !isfinite(s1)) { res->status = (int)DMRGC_ENUMERIC; k = k > 0 ? k : 1; }
     if (k < 1) k = 1;
     res->k = k;
@@ -240,7 +261,8 @@ __global__ void gather_kernel(const typename cplx<R>::T* __restrict__ W, int m, 
 size_t jacobi_ctl_bytes() { return sizeof(JacobiCtl); }
 
 cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
-                                 void* ctl, cudaStream_t st, int* launches) {
+                                 const double* fro2, double zero_rel, void* ctl, cudaStream_t st,
+                                 int* launches) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(JacobiCtl), st);
   if (e != cudaSuccess) return e;
   if (n < 2 || m < 1) return cudaSuccess;
@@ -259,14 +281,14 @@ cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, i
   if (blocks < 1) blocks = 1;
   JacobiCtl* c = reinterpret_cast<JacobiCtl*>(ctl);
   if (fp64) {
-    double tl = tol;
+    double tl = tol, zr = zero_rel;
     double2* g = reinterpret_cast<double2*>(G);
-    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, &c};
+    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, (void*)&fro2, &zr, &c};
     e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
   } else {
-    float tl = (float)tol;
+    float tl = (float)tol, zr = (float)zero_rel;
     float2* g = reinterpret_cast<float2*>(G);
-    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, &c};
+    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, (void*)&fro2, &zr, &c};
     e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
   }
   if (launches) *launches += 1;
@@ -278,7 +300,8 @@ size_t trunc_bytes(int n) {
 }
 
 cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, double rel_cut,
-                             bool squared, void* res, cudaStream_t st) {
+                             bool squared, double tie_rel, const double* fro2, double zero_rel,
+                             void* res, cudaStream_t st) {
   TruncResult* r = reinterpret_cast<TruncResult*>(res);
   double* s = reinterpret_cast<double*>(r + 1);
   int* perm = reinterpret_cast<int*>(s + n);
@@ -298,7 +321,8 @@ cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, do
     e = cudaFuncSetAttribute(sort_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  sort_trunc_kernel<<<1, 1024, sm, st>>>(r, s, perm, s, n, chi, rel_cut, squared ? 1 : 0);
+  sort_trunc_kernel<<<1, 1024, sm, st>>>(r, s, perm, s, n, chi, rel_cut, squared ? 1 : 0, tie_rel,
+                                         fro2, zero_rel);
   return cudaGetLastError();
 }
 
