@@ -1,0 +1,362 @@
+"""Benchmark: two-site updates/s of the circuit-DMRG compression sweep.
+
+Workload (N=1): 54 qubits on a 6x9 grid, Sycamore-like random circuit
+(sqrt(X/Y/W) + fSim(pi/2, pi/6), staggered ABCD-CDAB pattern), K = 2 cycles per
+compression step, chi = 512, 2 sweeps per step (2(N-1) = 106 two-site updates).
+One benchmark step = one compression step of the whole hot path: layer-MPO
+build, zip-up guess, 106 updates (theta, truncated SVD, environments).  The
+first --warmup steps grow the bond dimension to chi; the next --steps are timed.
+
+value: updates/s from CUDA events on the library's stream (gate records already
+packed); e2e: the same metric by wall clock through the C ABI with host
+buffers, including per step the gate upload, the fidelity read-back and the
+amplitudes of 1024 bit strings (host bits in, host amplitudes out).
+Inputs are far larger than L2 (environment caches of several GB), so no L2 flush.
+
+--impl reference times the CPU oracle on the host cores instead (one oracle
+update per step at a bulk bond of the same workload).
+
+Multi-GPU: one independent circuit instance per rank (the sweep of one circuit
+is sequential), weak scaling; timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "fp32": 3}
+DTYPE_NAME = {"fp64": "c128-f64", "bf16x3": "c64-bf16x3", "tf32x3": "c64-tf32x3", "fp32": "c64-f32"}
+FP32_LANES_PER_SM = 128
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (CUDA cores and tensor cores alike)
+N_SMS = 152
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(value_local: float, group_world: int, reduce_max):
+    """Max over ranks of a local time (reduce_max: callable or None for N=1)."""
+    if group_world <= 1 or reduce_max is None:
+        return value_local
+    return reduce_max(value_local)
+
+
+def alu_peak_tflops(fp64: bool, sm_mhz: float | None) -> float:
+    """CUDA-core FMA peak at the sampled SM clock: 152 SMs x 128 FP32 lanes x 2
+    flops x clock; FP64 uses the nominal 1.25 TFLOP/s scaled by the clock."""
+    mhz = sm_mhz or 2070.0
+    if fp64:
+        return FP64_PEAK_TFLOPS * mhz / 2070.0
+    return N_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(chi: int = 512, d_mpo: int = 64, seed: int = 0):
+    """One oracle two-site update at a bulk bond of the 54-qubit workload:
+    chi on both outer bonds, MPO bond D on the three cuts (a CD-layer bulk
+    bond), random isometric MPS tensors and random MPO tensors (the cost does
+    not depend on the values).  Returns (seconds, threads)."""
+    from oracle import dmrg as od
+    rng = np.random.default_rng(seed)
+
+    def rnd(*shape):
+        return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+    lenv = rnd(chi, d_mpo, chi)
+    renv = rnd(chi, d_mpo, chi)
+    b1 = rnd(chi, 2, chi)
+    b2 = rnd(chi, 2, chi)
+    w1 = rnd(d_mpo, 2, 2, d_mpo)
+    w2 = rnd(d_mpo, 2, 2, d_mpo)
+    t0 = time.perf_counter()
+    x = od.make_x(lenv, b1, w1)
+    y = od.make_y(renv, b2, w2)
+    th = od.theta_of(x, y)
+    u, s, vh, _ = od.svd_truncate(th, chi, 1e-12)
+    a1 = u.reshape(chi, 2, -1)
+    od.env_left(a1, x)
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count() or 1
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            threads = max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return dt, threads
+
+
+# ------------------------------------------------------------------- main
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2207_05612_gb300 import Context, binding
+    from synthetic import circuits as sc
+
+    reduce_max = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+        def reduce_max(v):
+            t = torch.tensor([v], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+
+    rows, cols = args.rows, args.cols
+    n = rows * cols
+    layers_needed = args.warmup + args.steps
+    cycles = max(20, 2 * layers_needed)
+    circ = sc.random_circuit(rows, cols, cycles, seed=args.seed + rank)
+    stream = torch.cuda.current_stream()
+    prec = PRECISIONS[args.precision]
+    ctx = Context(rows, cols, args.chi, precision=prec, timing=True, stream=stream.cuda_stream)
+    packed = [binding.pack_gates(l) for l in circ.layers[:args.warmup]]
+    bits = sc.random_bitstrings(n, 1024, seed=7)
+    upd_per_step = 2 * (n - 1)
+
+    # warm-up steps: grow the bonds to chi
+    for li in range(args.warmup):
+        binding._check(binding.lib().dmrgc_apply_layer(ctx.h, packed[li], len(circ.layers[li])), ctx.h)
+        ctx.sweep(2)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    h2d = d2h = 0
+    t_region0 = time.perf_counter()
+    for k in range(args.steps):
+        li = args.warmup + k
+        layer = circ.layers[li]
+        # one step through the public API from host data: gate records packed on
+        # the host and copied in by apply_layer; the device part (apply_layer +
+        # two sweeps) is bracketed by CUDA events; fidelity and 1024 amplitudes
+        # come back to the host
+        gates = binding.pack_gates(layer)
+        ev[2 * k].record(stream)
+        binding._check(binding.lib().dmrgc_apply_layer(ctx.h, gates, len(layer)), ctx.h)
+        ctx.sweep(2)
+        ev[2 * k + 1].record(stream)
+        ctx.fidelity()
+        amps = ctx.amplitude(bits)
+        h2d += len(layer) * 264 + bits.nbytes
+        d2h += amps.size * 16 + 16
+    torch.cuda.synchronize()
+    t_region = time.perf_counter() - t_region0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
+    st = ctx.stats()
+    dev_s = aggregate(dev_ms / 1e3, world, reduce_max)
+    region_s = aggregate(t_region, world, reduce_max)
+    total_updates = upd_per_step * args.steps * world
+    lf, fd = ctx.fidelity()
+    bonds, dmpo = ctx.bond_dims()
+    return {
+        "ctx": ctx, "dev_s": dev_s, "region_s": region_s, "updates": total_updates, "stats": st,
+        "clocks": clk, "h2d": h2d // args.steps, "d2h": d2h // args.steps, "log_ft": lf,
+        "f_delta": fd, "max_chi": max(bonds), "max_D": max(dmpo), "rank": rank,
+        "n2g": sum(1 for l in circ.layers[:args.warmup + args.steps] for g in l if g[1] >= 0),
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS))
+    ap.add_argument("--rows", type=int, default=6)
+    ap.add_argument("--cols", type=int, default=9)
+    ap.add_argument("--chi", type=int, default=512)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    world, rank, local = dist_setup()
+    workload = f"random circuit {args.rows}x{args.cols} ({args.rows * args.cols}q), K=2 cycles/step, chi={args.chi}, 2 sweeps"
+    config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
+              "cycles_per_step": 2, "sweeps_per_step": 2,
+              "updates_per_step": 2 * (args.rows * args.cols - 1),
+              "l2": "inputs larger than L2 (environment caches of GBs), no flush"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        times = []
+        threads = 1
+        for k in range(args.warmup + args.steps):
+            dt, threads = oracle_sample(args.chi, 64, seed=k)
+            if k >= args.warmup:
+                times.append(dt)
+        tot = sum(times)
+        value = args.steps / tot
+        sample = f"one oracle two-site update at a bulk bond (chi={args.chi} both sides, MPO bond 64), per step"
+        line = {"impl": "reference", "metric": "two-site updates/s", "value": value,
+                "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128-f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": "updates/s", "cores": threads,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    r = run_ours(args, world, rank, local)
+    if rank != 0:
+        return 0
+    st = r["stats"]
+    peaks, peak_src = measured_peaks()
+    value = r["updates"] / r["dev_s"]
+    e2e = r["updates"] / r["region_s"]
+    fp64 = args.precision == "fp64"
+    gemm_s, svd_s = st["gemm_ms"] / 1e3, st["svd_ms"] / 1e3
+    # dominant kernel class by device time
+    if st["gemm_ms"] >= st["svd_ms"]:
+        achieved = st["gemm_flops"] / max(gemm_s, 1e-12) / 1e12
+        dom = "complex GEMM (contractions)"
+        launches = st["gemm_launches"]
+    else:
+        achieved = st["svd_flops"] / max(svd_s, 1e-12) / 1e12
+        dom = "one-sided Jacobi SVD"
+        launches = st["svd_launches"]
+    clk = r["clocks"]
+    if args.precision in ("bf16x3", "tf32x3"):
+        ratio = 1.0 if args.precision == "bf16x3" else 0.5
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * ratio / 3.0
+        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_note": f"{peak_src} sustained bf16 x {ratio} / 3 split products"}
+    else:
+        peak = alu_peak_tflops(fp64, clk.get("sm_mhz"))
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": "CUDA-core FMA peak: 152 SMs x 128 FP32 lanes x 2 x sampled SM clock"
+                             if not fp64 else "nominal FP64 1.25 TFLOP/s x sampled/max SM clock"}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        dt, threads = oracle_sample(args.chi, 64)
+        cpu = {"value": 1.0 / dt, "unit": "updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"one oracle two-site update at a bulk bond (chi={args.chi} both sides, MPO bond 64), {dt:.1f} s"}
+    line = {
+        "metric": "two-site updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_NAME[args.precision], "data": "synthetic", "config": config,
+        "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                   "reasons": clk.get("reasons")},
+        "gpu_launches": int(st["kernel_launches"]),
+        "fidelity": {"log_F_tilde": r["log_ft"], "f_delta_last": r["f_delta"],
+                     "eps_tilde": float(1 - np.exp(r["log_ft"] / max(1, r["n2g"]))),
+                     "n_2q_gates": r["n2g"]},
+        "breakdown_ms": {"gemm": st["gemm_ms"], "svd": st["svd_ms"], "mpo": st["mpo_ms"],
+                         "other": st["other_ms"],
+                         "gemm_tflops": st["gemm_flops"] / max(gemm_s, 1e-12) / 1e12,
+                         "svd_tflops": st["svd_flops"] / max(svd_s, 1e-12) / 1e12,
+                         "jacobi_sweeps_per_svd": st["jacobi_sweeps"] / max(1, st["svd_launches"] / 4)},
+        "state": {"max_chi": r["max_chi"], "max_D": r["max_D"]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -85,7 +85,11 @@ typedef struct {
   double gemm_ms, gemm_flops;   /* all contractions (environments, X/Y, theta, Gram, gauge) */
   long long gemm_launches;
   double svd_ms;                /* Jacobi SVD incl. sort/gather */
+  double svd_flops;             /* algorithmic real flops of the Jacobi kernels: 16 per complex
+                                   element for the three dot products of every pair visited,
+                                   14 per element for every rotation applied */
   long long svd_launches;
+  long long jacobi_sweeps;      /* Jacobi sweeps executed (sum over SVDs) */
   double mpo_ms;                /* layer MPO build */
   double other_ms;              /* permutes, copies, norms */
   long long updates;            /* two-site updates done */

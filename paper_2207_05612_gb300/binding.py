@@ -42,7 +42,8 @@ class Gate(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("gemm_ms", C.c_double), ("gemm_flops", C.c_double), ("gemm_launches", C.c_longlong),
-                ("svd_ms", C.c_double), ("svd_launches", C.c_longlong), ("mpo_ms", C.c_double),
+                ("svd_ms", C.c_double), ("svd_flops", C.c_double), ("svd_launches", C.c_longlong),
+                ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
                 ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong)]
 
 

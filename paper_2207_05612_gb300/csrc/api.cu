@@ -259,7 +259,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
     c->stats.svd_launches += launches + 3;
     c->stats.kernel_launches += launches + 3;
   }
-  struct { int count, gen; unsigned off[2]; int err, sweeps, pad[2]; } ctl{};
+  struct { int count, gen; unsigned off[2]; int err, sweeps; unsigned long long rot; } ctl{};
   TruncResult tr{};
   CK(cudaMemcpyAsync(&ctl, c->jctl.p, sizeof(ctl), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(&tr, c->tres.p, sizeof(tr), cudaMemcpyDeviceToHost, c->st));
@@ -269,6 +269,8 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
     return fail(c, DMRGC_ENOCONV, "Jacobi SVD did not converge in " + std::to_string(c->max_jsweeps) + " sweeps");
   if (tr.status != 0 || !std::isfinite(tr.f) || !(tr.f > 0))
     return fail(c, DMRGC_ENUMERIC, "truncated SVD met a zero or non-finite spectrum");
+  c->stats.jacobi_sweeps += ctl.sweeps;
+  c->stats.svd_flops += (double)ctl.sweeps * 0.5 * n * (n - 1) * 16.0 * m + (double)ctl.rot * 14.0 * m;
   k = tr.k;
   f = tr.f;
   return DMRGC_OK;
@@ -976,7 +978,7 @@ dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int ch
       cudaSuccess)
     return DMRGC_ECUDA;
   TruncResult tr{};
-  struct { int count, gen; unsigned off[2]; int err, sweeps, pad[2]; } cs{};
+  struct { int count, gen; unsigned off[2]; int err, sweeps; unsigned long long rot; } cs{};
   if (cudaMemcpy(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
   if (cudaMemcpy(&cs, ctl, sizeof(cs), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
   if (cs.err == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;

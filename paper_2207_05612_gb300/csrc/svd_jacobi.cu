@@ -28,7 +28,7 @@ struct JacobiCtl {
   unsigned off_bits[2];   // float bits of the largest relative off-diagonal of a sweep
   int err;                // 0 ok, DMRGC_ETIMEOUT, DMRGC_ENOCONV
   int sweeps;             // sweeps executed
-  int pad[2];
+  unsigned long long rotations;   // rotations applied (for the flop count)
 };
 
 constexpr unsigned long long kSpinLimit = 20000000ull;  // x ~64 ns = ~1.3 s
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __rest
   const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
   const R tiny = (R)fmax(fz, (sizeof(R) == 8) ? 1e-280 : 1e-30);
   int sweep = 0;
+  unsigned long long rot = 0;
   for (; sweep < max_sweeps; ++sweep) {
     float local_off = 0.f;
     for (int r = 0; r < np - 1; ++r) {
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __rest
         const R rel = gabs / sqrt(al * be);
         if (!(rel > tol)) continue;
         local_off = fmaxf(local_off, (float)rel);
+        ++rot;
         // phase e^{-i phi} of gamma, real rotation on (u, e^{-i phi} v)
         const R er = gr / gabs, ei = -gi / gabs;
         const R zeta = (al - be) / (2 * gabs);
@@ -133,12 +135,16 @@ __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __rest
       if (lane == 0 && local_off > 0.f)
         atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(local_off));
       local_off = 0.f;
-      if (!grid_barrier(ctl, nb)) return;
+      if (!grid_barrier(ctl, nb)) {
+        if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+        return;
+      }
       if (r == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
     }
     const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
     if (!(off > (float)tol)) { ++sweep; break; }
   }
+  if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->sweeps = sweep;
     const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);

@@ -1,0 +1,61 @@
+"""Host-side logic of bench.py on CPU: the max-over-ranks timing with a
+world_size-2 gloo group, the clock-record parser, the ALU peak."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    def reduce_max(v):
+        t = torch.tensor([v], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    got = bench.aggregate(1.0 + rank, world, reduce_max)
+    out[rank] = got
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert out[0] == 2.0 and out[1] == 2.0
+
+
+def test_clock_parser_and_peaks():
+    import bench
+    c = bench.ClockSampler(0)
+    c.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0,
+                            "kill": lambda self: None})()
+    c.lines = ["0, 1500, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "0, 1700, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    r = c.stop()
+    assert r["sm_mhz"] == 1600.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
+    assert abs(bench.alu_peak_tflops(False, 2070.0) - 152 * 128 * 2 * 2.07e-3) < 1e-9
+    assert bench.alu_peak_tflops(True, 2070.0) == 1.25
