@@ -180,6 +180,37 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out);
 
+/* Truncated SVD of a device matrix that allocates no memory at all.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- for example code whose device memory is already fully
+ * claimed by its own caching allocator (an extra cudaMalloc would fail or
+ * break that allocator's budget), or latency-critical loops that must not
+ * pay the device-wide synchronisation cudaMalloc and cudaFree can cause.
+ * It runs the same one-sided Jacobi, truncation and gather kernels as the
+ * sweep, but its scratch -- the barrier block, |G|_F^2, the sorted spectrum
+ * and its permutation -- lives in a fixed 64 KiB array compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * G: device, complex (double2 for precision DMRGC_FP64, float2 otherwise),
+ *    m x n column-major; it is overwritten (on return its columns are G V).
+ * n: 2 .. 4096 columns (the array's limit); larger n returns DMRGC_EINVAL.
+ * s_out: device double[n], the singular values in descending order.
+ * U_out: device, m x k row-major in the same complex type (capacity m*min(chi,n)),
+ *        the kept left singular vectors; *k_out (host) = k = min(chi,
+ *        #{s > max(rel_cut*s_1, numerical zero)}).
+ * stream: cudaStream_t (NULL = default stream); the call synchronises it
+ *        before returning.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (the device must be current); make that first call
+ * before any stream capture.  All calls share the one array and leave their
+ * contents in it; the parts that must start at zero are cleared by each call.
+ * Calls that overlap on the GPU (several host threads, or several streams)
+ * race on the array: serialise them. */
+dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, int chi, double rel_cut,
+                               double* s_out, int* k_out, void* U_out, void* stream);
+
 const char* dmrgc_last_error(const dmrgc_ctx* ctx);
 void dmrgc_destroy(dmrgc_ctx* ctx);
 

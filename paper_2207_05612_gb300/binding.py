@@ -82,7 +82,9 @@ def lib():
                                       C.c_longlong, C.c_longlong, C.c_void_p]
         L.dmrgc_test_svd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                      C.c_void_p, P(C.c_int), C.c_void_p]
-        for name in ("dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+        L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                                        C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
+        for name in ("dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
             getattr(L, name).restype = C.c_int
@@ -223,6 +225,17 @@ def dmrgc_test_svd(precision: int, g: np.ndarray, chi: int, rel_cut: float):
                                 C.byref(k), u.ctypes.data))
     kk = k.value
     return s, kk, u.reshape(-1)[:m * kk].reshape(m, kk)
+
+
+def dmrgc_svd_noalloc(precision: int, g_ptr: int, m: int, n: int, chi: int, rel_cut: float,
+                      s_ptr: int, u_ptr: int, stream: int = 0) -> int:
+    """Truncated SVD of a device matrix without any allocation (device
+    pointers in and out; see include/dmrgc.h).  Returns k."""
+    k = C.c_int()
+    _check(lib().dmrgc_svd_noalloc(precision, m, n, C.c_void_p(g_ptr), chi, rel_cut,
+                                   C.c_void_p(s_ptr), C.byref(k), C.c_void_p(u_ptr),
+                                   C.c_void_p(stream)))
+    return k.value
 
 
 class Context:

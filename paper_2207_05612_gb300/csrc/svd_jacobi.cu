@@ -17,6 +17,8 @@
 // update and theta^+ for a right-to-left one.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dmrgc {
@@ -352,4 +354,84 @@ cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void*
   return cudaGetLastError();
 }
 
+// ---- truncated SVD that allocates nothing
+//
+// Same Jacobi + truncation + gather path as the sweep, but its scratch (the
+// barrier/convergence block, |G|_F^2 and the sorted spectrum with its
+// permutation) lives in one file-scope device array instead of memory from
+// cudaMalloc.  Host code must not pass the array's name to a kernel (on the
+// host it is only a stand-in symbol); it resolves the device address once per
+// device with cudaGetSymbolAddress, with that device current.
+
+namespace {
+
+constexpr int kNoAllocMaxCols = 4096;
+constexpr size_t kNoAllocBytes = 65536;   // >= 256 + trunc_bytes(kNoAllocMaxCols)
+static __device__ __align__(256) unsigned char g_svd_scratch[kNoAllocBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[256] = {};
+
+cudaError_t scratch_for_current_device(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_svd_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = reinterpret_cast<unsigned char*>(g_scratch_ptr[dev]);
+  return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace dmrgc
+
+extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, int chi,
+                                          double rel_cut, double* s_out, int* k_out, void* U_out,
+                                          void* stream) {
+  using namespace dmrgc;
+  static_assert(256 + sizeof(TruncResult) + (sizeof(double) + sizeof(int)) * kNoAllocMaxCols + 64 <=
+                    kNoAllocBytes,
+                "scratch array too small");
+  if (precision < 0 || precision > 3 || m < 1 || m > (1 << 20) || n < 2 || n > kNoAllocMaxCols ||
+      chi < 1 || !G || !s_out || !k_out || !U_out || !(rel_cut >= 0.0))
+    return DMRGC_EINVAL;
+  const bool fp64 = precision == DMRGC_FP64;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  if (scratch_for_current_device(&base) != cudaSuccess) return DMRGC_ECUDA;
+  void* ctl = base;                                   // JacobiCtl, cleared by the Jacobi launcher
+  double* fro2 = reinterpret_cast<double*>(base + 128);  // cleared by sum_abs2
+  void* res = base + 256;                             // TruncResult, s[n], perm[n]: written in full
+  const double eps = fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+  const double tol = 8.0 * eps * std::sqrt((double)m);
+  const double zero_rel = fp64 ? 1e-13 : 1e-5;
+  int launches = 0;
+  if (sum_abs2(G, (long long)m * n, fp64, fro2, st) != cudaSuccess) return DMRGC_ECUDA;
+  if (jacobi_orthogonalize(G, m, n, fp64, tol, 40, fro2, zero_rel, ctl, st, &launches) != cudaSuccess)
+    return DMRGC_ECUDA;
+  if (truncate_columns(G, m, n, fp64, chi, rel_cut, false, 0.0, fro2, zero_rel, res, st) != cudaSuccess)
+    return DMRGC_ECUDA;
+  JacobiCtl hc{};
+  TruncResult tr{};
+  if (cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return DMRGC_ECUDA;
+  if (hc.err == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;
+  if (hc.err == DMRGC_ENOCONV) return DMRGC_ENOCONV;
+  if (tr.status != 0) return DMRGC_ENUMERIC;
+  const double* s_dev = reinterpret_cast<const double*>(reinterpret_cast<const TruncResult*>(res) + 1);
+  if (cudaMemcpyAsync(s_out, s_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return DMRGC_ECUDA;
+  if (gather_columns(G, m, n, tr.k, res, false, 0, U_out, fp64, st) != cudaSuccess) return DMRGC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DMRGC_ECUDA;
+  *k_out = tr.k;
+  return DMRGC_OK;
+}
