@@ -51,7 +51,8 @@ struct dmrgc_ctx {
   std::vector<int> chiA, chiB, D;     // N+1 entries each
   std::vector<char> xyk;
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
-  DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d;
+  DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d, tcerr;
+  TcWork tcw;
   EnvRef L, R;
   int phase = 0;           // 0 created, 1 guess ready / sweeping
   int bond = 0, dir = -1;  // next update (bond, bond+1), dir -1 = right-to-left
@@ -163,22 +164,30 @@ void flush_timing(dmrgc_ctx* c) {
 dmrgc_status sync(dmrgc_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   flush_timing(c);
+  if (c->tcerr.p) {
+    int e = 0;
+    CK(cudaMemcpy(&e, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return fail(c, DMRGC_ETIMEOUT, "a tensor-core GEMM wait timed out");
+  }
   return DMRGC_OK;
 }
 
 // ---- GEMM dispatch
 
-cudaError_t run_gemm(int precision, const GemmArgs& g, cudaStream_t st) {
-  if (precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3) return cudaErrorNotSupported;
+cudaError_t run_gemm(int precision, const GemmArgs& g, TcWork* w, int* err_dev, cudaStream_t st) {
+  if (precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3) return gemm_tc(g, precision, *w, err_dev, st);
   return gemm_simt(g, precision == DMRGC_FP64, st);
 }
 
 dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
-  if (c->opt.precision == DMRGC_BF16X3 || c->opt.precision == DMRGC_TF32X3)
-    return fail(c, DMRGC_EINVAL, "tensor-core precision modes are not available in this build");
+  const bool tc = c->opt.precision == DMRGC_BF16X3 || c->opt.precision == DMRGC_TF32X3;
+  if (tc && !c->tcerr.p) {
+    TRY(ensure(c, c->tcerr, 64));
+    CK(cudaMemsetAsync(c->tcerr.p, 0, 64, c->st));
+  }
   const double fl = 8.0 * g.M * (double)g.N * g.K * g.b1 * g.b2;
   Span sp(c, TC_GEMM, fl);
-  CK(run_gemm(c->opt.precision, g, c->st));
+  CK(run_gemm(c->opt.precision, g, &c->tcw, (int*)c->tcerr.p, c->st));
   c->stats.gemm_launches++;
   c->stats.kernel_launches++;
   return DMRGC_OK;
@@ -621,8 +630,9 @@ dmrgc_ctx::~dmrgc_ctx() {
   for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
-                    &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d})
+                    &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr})
     fr(*b);
+  tcw.release();
   for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : pool) cudaEventDestroy(e);
 }
@@ -947,9 +957,16 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
   g.A = dA; g.lda = lda; g.opA = opA;
   g.B = dB; g.ldb = ldb; g.opB = opB;
   g.C = dC; g.ldc = N;
-  cudaError_t e = run_gemm(precision, g, 0);
-  if (e == cudaErrorNotSupported) return DMRGC_EINVAL;
+  int* err = (int*)s.get(sizeof(int));
+  if (!err || cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return DMRGC_ENOMEM;
+  TcWork w;
+  cudaError_t e = run_gemm(precision, g, &w, err, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  w.release();
   if (e != cudaSuccess) return DMRGC_ECUDA;
+  if (herr) return DMRGC_ETIMEOUT;
   if (download_from(dC, (long long)M * N, fp64, s, C) != cudaSuccess) return DMRGC_ECUDA;
   return cudaDeviceSynchronize() == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
 }

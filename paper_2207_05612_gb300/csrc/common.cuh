@@ -49,6 +49,16 @@ struct GemmArgs {
 
 cudaError_t gemm_simt(const GemmArgs& g, bool fp64, cudaStream_t st);
 
+// Tensor-core path (complex64 data): packed split operands live in TcWork.
+// err_dev: device int set to DMRGC_ETIMEOUT if a bounded wait ran out.
+struct TcWork {
+  void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t cap[4] = {0, 0, 0, 0};
+  cudaError_t ensure(int i, size_t bytes);
+  void release();
+};
+cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, cudaStream_t st);
+
 // --------------------------------------------------------------------- SVD
 
 // One-sided (Hestenes) Jacobi on the columns of G (column-major, m x n,

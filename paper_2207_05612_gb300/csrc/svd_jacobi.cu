@@ -154,6 +154,95 @@ __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __rest
   }
 }
 
+// Register-resident variant for m <= 128*E: one CTA (128 threads) per column
+// pair, each thread holding E elements of both columns, so a pair costs one
+// load, one block reduction and one store.  Same rotation and stopping rule.
+template <typename R, int E>
+__global__ void __launch_bounds__(128) jacobi_reg_kernel(typename cplx<R>::T* __restrict__ G, int m,
+                                                         int n, int np, R tol, int max_sweeps,
+                                                         const double* __restrict__ fro2, R zero_rel,
+                                                         JacobiCtl* ctl) {
+  using C2 = typename cplx<R>::T;
+  __shared__ R red[2][4][4];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned nb = gridDim.x;
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const R tiny = (R)fmax(fz, (sizeof(R) == 8) ? 1e-280 : 1e-30);
+  int sweep = 0, buf = 0;
+  unsigned long long rot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int p = blockIdx.x; p < np / 2; p += gridDim.x) {
+        int a, b;
+        round_robin_pair(r, p, np, a, b);
+        if (a >= n || b >= n) continue;
+        C2* u = G + (long long)a * m;
+        C2* v = G + (long long)b * m;
+        C2 x[E], y[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = tid + e * 128;
+          if (i < m) { x[e] = u[i]; y[e] = v[i]; }
+          else { x[e] = C2{0, 0}; y[e] = C2{0, 0}; }
+        }
+        R al = 0, be = 0, gr = 0, gi = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          al += x[e].x * x[e].x + x[e].y * x[e].y;
+          be += y[e].x * y[e].x + y[e].y * y[e].y;
+          gr += x[e].x * y[e].x + x[e].y * y[e].y;
+          gi += x[e].x * y[e].y - x[e].y * y[e].x;
+        }
+        al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+        if (lane == 0) { red[buf][wid][0] = al; red[buf][wid][1] = be; red[buf][wid][2] = gr; red[buf][wid][3] = gi; }
+        __syncthreads();
+        al = red[buf][0][0] + red[buf][1][0] + red[buf][2][0] + red[buf][3][0];
+        be = red[buf][0][1] + red[buf][1][1] + red[buf][2][1] + red[buf][3][1];
+        gr = red[buf][0][2] + red[buf][1][2] + red[buf][2][2] + red[buf][3][2];
+        gi = red[buf][0][3] + red[buf][1][3] + red[buf][2][3] + red[buf][3][3];
+        buf ^= 1;   // the next pair reduces into the other buffer: no second barrier
+        const R gabs = sqrt(gr * gr + gi * gi);
+        if (al <= tiny || be <= tiny || gabs <= tiny) continue;
+        const R rel = gabs / sqrt(al * be);
+        if (!(rel > tol)) continue;
+        local_off = fmaxf(local_off, (float)rel);
+        if (tid == 0) ++rot;
+        const R er = gr / gabs, ei = -gi / gabs;
+        const R zeta = (al - be) / (2 * gabs);
+        const R sg = zeta >= 0 ? R(1) : R(-1);
+        const R t = -sg / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        const R c = R(1) / sqrt(R(1) + t * t);
+        const R sn = c * t;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = tid + e * 128;
+          if (i < m) {
+            const C2 ye{y[e].x * er - y[e].y * ei, y[e].x * ei + y[e].y * er};
+            u[i] = C2{c * x[e].x - sn * ye.x, c * x[e].y - sn * ye.y};
+            v[i] = C2{sn * x[e].x + c * ye.x, sn * x[e].y + c * ye.y};
+          }
+        }
+      }
+      if (tid == 0 && local_off > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(local_off));
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) {
+        if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
+        return;
+      }
+      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > (float)tol)) { ++sweep; break; }
+  }
+  if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > (float)tol && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
 // ---- column norms, sort, truncation rank
 
 template <typename R>
@@ -268,37 +357,52 @@ __global__ void gather_kernel(const typename cplx<R>::T* __restrict__ W, int m, 
 
 size_t jacobi_ctl_bytes() { return sizeof(JacobiCtl); }
 
+namespace {
+
+template <typename R>
+cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, const double* fro2,
+                          double zero_rel, JacobiCtl* c, cudaStream_t st) {
+  using C2 = typename cplx<R>::T;
+  const int np = (n + 1) & ~1;
+  const int pairs = np / 2;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* fn;
+  int threads = 128, blocks;
+  if (m <= 128 * 16) {
+    if (m <= 128 * 2) fn = (void*)jacobi_reg_kernel<R, 2>;
+    else if (m <= 128 * 4) fn = (void*)jacobi_reg_kernel<R, 4>;
+    else if (m <= 128 * 8) fn = (void*)jacobi_reg_kernel<R, 8>;
+    else fn = (void*)jacobi_reg_kernel<R, 16>;
+    blocks = pairs;   // one CTA per pair
+  } else {
+    fn = (void*)jacobi_kernel<R>;
+    blocks = (pairs + threads / 32 - 1) / (threads / 32);
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+  if (e != cudaSuccess) return e;
+  const int cap = sms * per_sm;   // every CTA of a cooperative launch must be resident
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  C2* g = reinterpret_cast<C2*>(G);
+  R tl = (R)tol, zr = (R)zero_rel;
+  int mm = m, nn = n, npp = np, ms = max_sweeps;
+  void* args[] = {&g, &mm, &nn, &npp, &tl, &ms, (void*)&fro2, &zr, &c};
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
+}
+
+}  // namespace
+
 cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
                                  const double* fro2, double zero_rel, void* ctl, cudaStream_t st,
                                  int* launches) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(JacobiCtl), st);
   if (e != cudaSuccess) return e;
   if (n < 2 || m < 1) return cudaSuccess;
-  const int np = (n + 1) & ~1;
-  const int threads = 128;
-  const int pairs = np / 2;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  void* fn = fp64 ? (void*)jacobi_kernel<double> : (void*)jacobi_kernel<float>;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
-  if (e != cudaSuccess) return e;
-  int blocks = (pairs + threads / 32 - 1) / (threads / 32);
-  const int cap = sms * (per_sm < 2 ? per_sm : 2);
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
   JacobiCtl* c = reinterpret_cast<JacobiCtl*>(ctl);
-  if (fp64) {
-    double tl = tol, zr = zero_rel;
-    double2* g = reinterpret_cast<double2*>(G);
-    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, (void*)&fro2, &zr, &c};
-    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
-  } else {
-    float tl = (float)tol, zr = (float)zero_rel;
-    float2* g = reinterpret_cast<float2*>(G);
-    void* args[] = {&g, &m, &n, (void*)&np, &tl, &max_sweeps, (void*)&fro2, &zr, &c};
-    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
-  }
+  e = fp64 ? launch_jacobi<double>(G, m, n, tol, max_sweeps, fro2, zero_rel, c, st)
+           : launch_jacobi<float>(G, m, n, tol, max_sweeps, fro2, zero_rel, c, st);
   if (launches) *launches += 1;
   return e;
 }

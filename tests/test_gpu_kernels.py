@@ -17,7 +17,12 @@ def _rand(rng, shape):
     return rng.normal(size=shape) + 1j * rng.normal(size=shape)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 2e-5)])
+# BF16x3: each operand is hi + lo with 16 significant bits (2^-17 relative),
+# products ~1.5e-5 relative; TF32x3: ~2^-22 per operand.  FP32 accumulation.
+GEMM_TOL = [(0, 1e-12), (3, 2e-5), (1, 5e-5), (2, 5e-6)]
+
+
+@pytest.mark.parametrize("prec,tol", GEMM_TOL)
 @pytest.mark.parametrize("op_a", [0, 1, 2, 3])
 @pytest.mark.parametrize("op_b", [0, 1, 2, 3])
 def test_gemm_ops(prec, tol, op_a, op_b):
@@ -31,16 +36,16 @@ def test_gemm_ops(prec, tol, op_a, op_b):
     assert np.abs(got - want).max() <= tol * np.abs(want).max() * np.sqrt(k)
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_gemm_large_k(prec):
+@pytest.mark.parametrize("prec,tol", GEMM_TOL)
+@pytest.mark.parametrize("m,n,k", [(130, 70, 300), (300, 257, 1000), (8, 8, 4000)])
+def test_gemm_large_k(prec, tol, m, n, k):
+    """Several M/N tiles, ragged edges, and K long enough for split-K."""
     from paper_2207_05612_gb300 import binding
-    rng = np.random.default_rng(3)
-    m, n, k = 130, 70, 300
+    rng = np.random.default_rng(3 + k)
     a = _rand(rng, (m, k))
     b = _rand(rng, (n, k))
     want = a @ b.T
     got = binding.dmrgc_test_gemm(prec, a, b, 0, 1, m, n, k)
-    tol = 1e-12 if prec == 0 else 2e-5
     assert np.abs(got - want).max() <= tol * np.abs(want).max() * np.sqrt(k)
 
 
