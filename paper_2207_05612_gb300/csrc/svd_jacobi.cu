@@ -243,6 +243,151 @@ __global__ void __launch_bounds__(128) jacobi_reg_kernel(typename cplx<R>::T* __
   }
 }
 
+// Blocked variant (complex64, m <= 128*E): the columns form blocks of 4 and
+// the blocks follow the round-robin order.  In a block round a CTA holds two
+// blocks (8 columns) in registers and rotates all 16 cross pairs in 4
+// sub-rounds of 4 disjoint pairs -- plus, in the first block round of a sweep,
+// the 6 intra-block pairs of each of its blocks -- so one grid barrier covers
+// 16 pair rotations and a sweep needs n/4 - 1 barriers instead of n - 1.  Every
+// column pair still meets exactly once per sweep (cyclic Jacobi reordered).
+template <int SUB, int E>
+__device__ __forceinline__ void blk_subround(float2 (&x)[8][E], const bool (&valid)[8], float (&red)[2][4][16],
+                                             int& buf, float tiny, float tol, float& local_off,
+                                             unsigned long long& rot) {
+  // sub-rounds 0-2: intra-block pairs (block I = slots 0..3, block J = slots 4..7);
+  // 3-6: cross pairs, slot q of I with slot (q + s) mod 4 of J
+  constexpr int P[7][4][2] = {{{0, 1}, {2, 3}, {4, 5}, {6, 7}}, {{0, 2}, {1, 3}, {4, 6}, {5, 7}},
+                              {{0, 3}, {1, 2}, {4, 7}, {5, 6}}, {{0, 4}, {1, 5}, {2, 6}, {3, 7}},
+                              {{0, 5}, {1, 6}, {2, 7}, {3, 4}}, {{0, 6}, {1, 7}, {2, 4}, {3, 5}},
+                              {{0, 7}, {1, 4}, {2, 5}, {3, 6}}};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float acc[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float2 a = x[P[SUB][k][0]][e], b = x[P[SUB][k][1]][e];
+      al += a.x * a.x + a.y * a.y;
+      be += b.x * b.x + b.y * b.y;
+      gr += a.x * b.x + a.y * b.y;
+      gi += a.x * b.y - a.y * b.x;
+    }
+    acc[k][0] = al; acc[k][1] = be; acc[k][2] = gr; acc[k][3] = gi;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[k][q] = warp_sum(acc[k][q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[buf][wid][4 * k + q] = acc[k][q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      acc[k][q] = red[buf][0][4 * k + q] + red[buf][1][4 * k + q] + red[buf][2][4 * k + q] + red[buf][3][4 * k + q];
+  buf ^= 1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int ia = P[SUB][k][0], ib = P[SUB][k][1];
+    if (!valid[ia] || !valid[ib]) continue;
+    const float al = acc[k][0], be = acc[k][1], gr = acc[k][2], gi = acc[k][3];
+    const float gabs = sqrtf(gr * gr + gi * gi);
+    if (al <= tiny || be <= tiny || gabs <= tiny) continue;
+    const float rel = gabs / sqrtf(al * be);
+    if (!(rel > tol)) continue;
+    local_off = fmaxf(local_off, rel);
+    if (threadIdx.x == 0) ++rot;
+    const float er = gr / gabs, ei = -gi / gabs;
+    const float zeta = (al - be) / (2.f * gabs);
+    const float sg = zeta >= 0.f ? 1.f : -1.f;
+    const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+    const float c = 1.f / sqrtf(1.f + t * t);
+    const float sn = c * t;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float2 xa = x[P[SUB][k][0]][e], yb = x[P[SUB][k][1]][e];
+      const float2 ye{yb.x * er - yb.y * ei, yb.x * ei + yb.y * er};
+      x[P[SUB][k][0]][e] = float2{c * xa.x - sn * ye.x, c * xa.y - sn * ye.y};
+      x[P[SUB][k][1]][e] = float2{sn * xa.x + c * ye.x, sn * xa.y + c * ye.y};
+    }
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(128, 2) jacobi_blk_kernel(float2* __restrict__ G, int m, int n, int nblk,
+                                                            float tol, int max_sweeps,
+                                                            const double* __restrict__ fro2, float zero_rel,
+                                                            JacobiCtl* ctl) {
+  __shared__ float red[2][4][16];
+  const int tid = threadIdx.x;
+  const unsigned nb = gridDim.x;
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const float tiny = (float)fmax(fz, 1e-30);
+  int sweep = 0, buf = 0;
+  unsigned long long rot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < nblk - 1; ++r) {
+      for (int p = blockIdx.x; p < nblk / 2; p += gridDim.x) {
+        int I, J;
+        round_robin_pair(r, p, nblk, I, J);
+        int col[8];
+        bool valid[8];
+        float2 x[8][E];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          col[q] = (q < 4 ? I : J) * 4 + (q & 3);
+          valid[q] = col[q] < n;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = tid + e * 128;
+            x[q][e] = (valid[q] && i < m) ? G[(long long)col[q] * m + i] : float2{0.f, 0.f};
+          }
+        }
+        if (r == 0) {
+          blk_subround<0, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+          blk_subround<1, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+          blk_subround<2, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+        }
+        blk_subround<3, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+        blk_subround<4, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+        blk_subround<5, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+        blk_subround<6, E>(x, valid, red, buf, tiny, tol, local_off, rot);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (!valid[q]) continue;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = tid + e * 128;
+            if (i < m) G[(long long)col[q] * m + i] = x[q][e];
+          }
+        }
+      }
+      if (tid == 0 && local_off > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(local_off));
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) {
+        if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
+        return;
+      }
+      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > tol)) { ++sweep; break; }
+  }
+  if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > tol && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
 // ---- column norms, sort, truncation rank
 
 template <typename R>
@@ -370,7 +515,16 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   void* fn;
   int threads = 128, blocks;
-  if (m <= 128 * 16) {
+  const bool blocked = sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
+  int nblk = 0;
+  if (blocked) {
+    nblk = (n + 3) / 4;
+    nblk += nblk & 1;
+    if (m <= 128 * 2) fn = (void*)jacobi_blk_kernel<2>;
+    else if (m <= 128 * 4) fn = (void*)jacobi_blk_kernel<4>;
+    else fn = (void*)jacobi_blk_kernel<8>;
+    blocks = nblk / 2;
+  } else if (m <= 128 * 16) {
     if (m <= 128 * 2) fn = (void*)jacobi_reg_kernel<R, 2>;
     else if (m <= 128 * 4) fn = (void*)jacobi_reg_kernel<R, 4>;
     else if (m <= 128 * 8) fn = (void*)jacobi_reg_kernel<R, 8>;
@@ -387,7 +541,7 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   if (blocks < 1) blocks = 1;
   C2* g = reinterpret_cast<C2*>(G);
   R tl = (R)tol, zr = (R)zero_rel;
-  int mm = m, nn = n, npp = np, ms = max_sweeps;
+  int mm = m, nn = n, npp = blocked ? nblk : np, ms = max_sweeps;
   void* args[] = {&g, &mm, &nn, &npp, &tl, &ms, (void*)&fro2, &zr, &c};
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
 }
