@@ -47,7 +47,9 @@ struct dmrgc_ctx {
   double sweep_cut = 1e-12, zip_cut = 1e-5, zero_rel = 1e-13, tie_rel = 1e-10;
   int max_jsweeps = 40;
   std::vector<int> order, site_of;
-  std::vector<DevBuf> A, B, Wx, Wy, XY, E;
+  std::vector<DevBuf> A, B, Wx, Wy, XY, E, warm;
+  std::vector<int> warm_dim;   // per bond: dimension of the stored singular basis (0 = none)
+  std::vector<char> warm_side; // 'L': (a s1) basis from a left-to-right SVD; 'R': (s2 c) basis
   std::vector<int> chiA, chiB, D;     // N+1 entries each
   std::vector<char> xyk;
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
@@ -252,7 +254,7 @@ double jacobi_tol(const dmrgc_ctx* c, int m) {
 // squared: jw is a Gram matrix (its column norms are s^2); tie_rel > 0 applies
 // the multiplet rule at the cut.
 dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, double tie_rel,
-                         int& k, double& f) {
+                         int& k, double& f, int* nnz = nullptr) {
   TRY(ensure(c, c->jctl, jacobi_ctl_bytes()));
   TRY(ensure(c, c->tres, trunc_bytes(n)));
   TRY(ensure(c, c->scal, 64));
@@ -282,6 +284,28 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   c->stats.svd_flops += (double)ctl.sweeps * 0.5 * n * (n - 1) * 16.0 * m + (double)ctl.rot * 14.0 * m;
   k = tr.k;
   f = tr.f;
+  if (nnz) *nnz = tr.nnz;
+  return DMRGC_OK;
+}
+
+// Warm start of the Jacobi iteration at a bond.  Consecutive visits of a bond
+// come from opposite directions, and the basis on the side that has not changed
+// since the last visit is exactly the singular basis that SVD computed (left
+// vectors U after a left-to-right update, right vectors V after a
+// right-to-left one).  Rotating the Jacobi input by it leaves a nearly
+// orthogonal set of columns, so few sweeps remain.  Only complete bases (as
+// many vectors as the space's dimension) are stored; the rotation is unitary,
+// so the SVD it leads to is the same.
+dmrgc_status warm_store(dmrgc_ctx* c, int bond, char side, int dim, int ncols, int nnz) {
+  c->warm_dim[bond] = 0;
+  if (c->fp64 || nnz != dim || dim < 16) return DMRGC_OK;   // FP64 runs keep the plain iteration
+  TRY(ensure(c, c->warm[bond], (size_t)dim * dim * c->esz));
+  Span sp(c, TC_SVD);
+  // the first `dim` sorted columns of jw, normalised, column-major [dim x dim]
+  CK(gather_columns(c->jw.p, dim, ncols, dim, c->tres.p, false, 1, c->warm[bond].p, c->fp64, c->st));
+  c->stats.kernel_launches++;
+  c->warm_dim[bond] = dim;
+  c->warm_side[bond] = side;
   return DMRGC_OK;
 }
 
@@ -310,14 +334,22 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   int mrow, ncol;
   TRY(form_theta(c, i, mrow, ncol));
   TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-  {
+  if (c->warm_dim[i] == ncol && c->warm_side[i] == 'R') {
+    GemmArgs g;   // jw (column-major) = theta V_prev: row-major [ncol][mrow] = V^T theta^T
+    g.M = ncol; g.N = mrow; g.K = ncol;
+    g.A = c->warm[i].p; g.lda = ncol; g.opA = OP_N;
+    g.B = c->theta.p; g.ldb = ncol; g.opB = OP_T;
+    g.C = c->jw.p; g.ldc = mrow;
+    TRY(gemm(c, g));
+  } else {
     Span sp(c, TC_OTHER);
     CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
     c->stats.kernel_launches++;
   }
-  int k;
+  int k, nnz = 0;
   double f;
-  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f));
+  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
+  TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
   {
     Span sp(c, TC_SVD);
@@ -359,15 +391,23 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   int mrow, ncol;
   TRY(form_theta(c, i, mrow, ncol));
   TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-  {
+  if (c->warm_dim[i] == mrow && c->warm_side[i] == 'L') {
+    GemmArgs g;   // jw (column-major) = theta^+ U_prev: row-major [mrow][ncol] = U^T conj(theta)
+    g.M = mrow; g.N = ncol; g.K = mrow;
+    g.A = c->warm[i].p; g.lda = mrow; g.opA = OP_N;
+    g.B = c->theta.p; g.ldb = ncol; g.opB = OP_R;
+    g.C = c->jw.p; g.ldc = ncol;
+    TRY(gemm(c, g));
+  } else {
     Span sp(c, TC_OTHER);
     CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
     c->stats.kernel_launches++;
   }
-  int k;
+  int k, nnz = 0;
   double f;
   // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
-  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f));
+  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
+  TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
   {
     Span sp(c, TC_SVD);
@@ -627,7 +667,7 @@ dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
 
 dmrgc_ctx::~dmrgc_ctx() {
   auto fr = [](DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; };
-  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E})
+  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &warm})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
                     &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr})
@@ -680,6 +720,7 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
   for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
   c->A.resize(n_qubits); c->B.resize(n_qubits); c->Wx.resize(n_qubits); c->Wy.resize(n_qubits);
   c->XY.resize(n_qubits); c->E.resize(n_qubits); c->xyk.assign(n_qubits, 0);
+  c->warm.resize(n_qubits); c->warm_dim.assign(n_qubits, 0); c->warm_side.assign(n_qubits, 0);
   c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);
   dmrgc_status s = ensure(c, c->one, 64);
   if (s == DMRGC_OK) {
@@ -710,6 +751,7 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
     c->chiB = c->chiA;
   }
   c->hist.clear();
+  std::fill(c->warm_dim.begin(), c->warm_dim.end(), 0);
   TRY(build_mpo(c, gates, n_gates));
   std::fill(c->xyk.begin(), c->xyk.end(), 0);
   TRY(zip_guess(c));

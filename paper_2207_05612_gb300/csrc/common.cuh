@@ -83,6 +83,8 @@ struct TruncResult {
   int pad;        // 1: the cut fell in a multiplet reaching s_1 (kept at chi, not unique)
   double f;       // sum of kept s^2
   double norm2;   // sum of all s^2
+  int nnz;        // columns above the numerical-zero level (the rank found)
+  int pad2;
 };
 size_t trunc_bytes(int n);  // TruncResult followed by double s[n], int perm[n]
 // fro2 / zero_rel: the Frobenius norm^2 of the matrix given to the Jacobi kernel

@@ -50,7 +50,7 @@ __device__ __forceinline__ bool grid_barrier(JacobiCtl* c, unsigned nblocks) {
     } else {
       unsigned long long it = 0;
       while (*vgen == g) {
-        __nanosleep(64);
+        if (it > 4096) __nanosleep(64);
         if (*verr != 0) break;
         if (++it > kSpinLimit) {
           atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
@@ -388,6 +388,348 @@ __global__ void __launch_bounds__(128, 2) jacobi_blk_kernel(float2* __restrict__
   }
 }
 
+// Warp-pair variant (complex64, m <= 32*E): a CTA of 16 warps holds two
+// blocks of 8 columns, one column per warp in registers (lane l owns rows
+// l, l+32, ...).  In a sub-round the 16 warps form 8 disjoint pairs; the two
+// warps of a pair swap columns through shared memory, each computes the same
+// alpha, beta, gamma with warp shuffles only, and each applies its half of the
+// rotation to its own column.  One grid barrier separates block rounds
+// (column blocks move between CTAs in round-robin order).
+template <int SUB>
+__device__ __forceinline__ int wp_partner(int w) {
+  if (SUB < 7) {
+    // circle method on the 8 slots of each block: slot 0 fixed, slot q >= 1 at
+    // rotation position x = (q - 1 - SUB) mod 7; positions x and 7 - x pair up,
+    // position 0 pairs with slot 0
+    const int blk = w >> 3, q = w & 7;
+    int partner;
+    if (q == 0) {
+      partner = SUB % 7 + 1;
+    } else {
+      const int x = ((q - 1 - SUB) % 7 + 7) % 7;
+      partner = (x == 0) ? 0 : ((7 - x) + SUB) % 7 + 1;
+    }
+    return blk * 8 + partner;
+  }
+  const int s = SUB - 7;   // cross: slot q of block I with slot (q + s) mod 8 of block J
+  return w < 8 ? 8 + ((w + s) & 7) : ((w - 8 - s) & 7);
+}
+
+template <int E>
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int SUB, int E>
+__device__ __forceinline__ void wp_subround(float2 (&x)[E], bool valid_me, const bool* valid_all, float2* sbuf,
+                                            int m, float tiny, float tol, float& local_off,
+                                            unsigned long long& rot) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = wp_partner<SUB>(w);
+  const bool first = w < p;                 // the pair's first column is the lower slot
+  // own column to shared memory; the partner's column is then read from there
+  // (twice, so that only one column lives in registers); the closing barrier
+  // keeps the next sub-round from overwriting a column still being read
+  float2* mine = sbuf + (long long)w * m;
+  const float2* theirs = sbuf + (long long)p * m;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane + 32 * e;
+    if (i < m) mine[i] = x[e];
+  }
+  __syncthreads();
+  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;   // (u, v) = (first, second) column
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane + 32 * e;
+    const float2 y = (i < m) ? theirs[i] : float2{0.f, 0.f};
+    const float2 u = first ? x[e] : y;
+    const float2 v = first ? y : x[e];
+    al += u.x * u.x + u.y * u.y;
+    be += v.x * v.x + v.y * v.y;
+    gr += u.x * v.x + u.y * v.y;
+    gi += u.x * v.y - u.y * v.x;
+  }
+  al = warp_allsum<E>(al);
+  be = warp_allsum<E>(be);
+  gr = warp_allsum<E>(gr);
+  gi = warp_allsum<E>(gi);
+  const float gabs = sqrtf(gr * gr + gi * gi);
+  bool do_rot = valid_me && valid_all[p] && al > tiny && be > tiny && gabs > tiny;
+  float rel = 0.f;
+  if (do_rot) {
+    rel = gabs / sqrtf(al * be);
+    do_rot = rel > tol;
+  }
+  if (do_rot) {
+    if (first) {
+      local_off = fmaxf(local_off, rel);
+      if (lane == 0) ++rot;
+    }
+    const float er = gr / gabs, ei = -gi / gabs;
+    const float zeta = (al - be) / (2.f * gabs);
+    const float sg = zeta >= 0.f ? 1.f : -1.f;
+    const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+    const float c = 1.f / sqrtf(1.f + t * t);
+    const float sn = c * t;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = lane + 32 * e;
+      const float2 y = (i < m) ? theirs[i] : float2{0.f, 0.f};
+      const float2 u = first ? x[e] : y;
+      const float2 v = first ? y : x[e];
+      const float2 ve{v.x * er - v.y * ei, v.x * ei + v.y * er};
+      x[e] = first ? float2{c * u.x - sn * ve.x, c * u.y - sn * ve.y}
+                   : float2{sn * u.x + c * ve.x, sn * u.y + c * ve.y};
+    }
+  }
+  __syncthreads();
+}
+
+template <int E>
+__global__ void __launch_bounds__(512, 1) jacobi_wp_kernel(float2* __restrict__ G, int m, int n, int nblk,
+                                                           float tol, int max_sweeps,
+                                                           const double* __restrict__ fro2, float zero_rel,
+                                                           JacobiCtl* ctl) {
+  extern __shared__ float2 sbuf[];          // 16 columns x m
+  __shared__ bool valid_all[16];
+  __shared__ float off_w[16];
+  __shared__ unsigned long long rot_w[16];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const unsigned nb = gridDim.x;
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const float tiny = (float)fmax(fz, 1e-30);
+  const float conv = fmaxf(tol, 2e-4f);   // stop when a sweep's largest rotation is below conv
+  int sweep = 0;
+  unsigned long long rot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < nblk - 1; ++r) {
+      for (int pb = blockIdx.x; pb < nblk / 2; pb += gridDim.x) {
+        int I, J;
+        round_robin_pair(r, pb, nblk, I, J);
+        const int col = (w < 8 ? I : J) * 8 + (w & 7);
+        const bool valid = col < n;
+        if (lane == 0) valid_all[w] = valid;
+        float2 x[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = (valid && i < m) ? G[(long long)col * m + i] : float2{0.f, 0.f};
+        }
+        __syncthreads();
+        if (r == 0) {
+          wp_subround<0, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<1, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<2, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<3, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<4, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<5, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+          wp_subround<6, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        }
+        wp_subround<7, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<8, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<9, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<10, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<11, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<12, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<13, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        wp_subround<14, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
+        if (valid) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            if (i < m) G[(long long)col * m + i] = x[e];
+          }
+        }
+        __syncthreads();   // valid_all and sbuf are reused by the next pair of blocks
+      }
+      if (lane == 0) off_w[w] = local_off;
+      __syncthreads();
+      if (tid == 0) {
+        float mx = 0.f;
+        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, off_w[i]);
+        if (mx > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(mx));
+      }
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) {
+        if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+        return;
+      }
+      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > conv)) { ++sweep; break; }
+  }
+  if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+  (void)rot_w;
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > conv && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
+// Warp-pair variant with 4-column blocks (complex64, m <= 32*E): 8 warps per
+// CTA, so that 128 CTAs cover n = 1024 (the 8-column version left most SMs
+// idle); both columns of a pair live in registers, the column exchange is
+// double buffered (one CTA barrier per sub-round), and each warp runs the code
+// of its role without per-element selects.
+template <int SUB>
+__device__ __forceinline__ int wp4_partner(int w) {
+  if (SUB < 3) {   // intra-block: (0,1)(2,3) / (0,2)(1,3) / (0,3)(1,2) in both blocks
+    const int blk = w >> 2, q = w & 3;
+    const int pr = SUB == 0 ? (q ^ 1) : SUB == 1 ? (q ^ 2) : (3 - q);
+    return blk * 4 + pr;
+  }
+  const int s = SUB - 3;   // cross: slot q of block I with slot (q + s) mod 4 of block J
+  return w < 4 ? 4 + ((w + s) & 3) : ((w - 4 - s) & 3);
+}
+
+template <bool FIRST, int E>
+__device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], bool ok, float tiny, float tol,
+                                         float& local_off, unsigned long long& rot) {
+  // (u, v) = (first, second) column: the same arithmetic in both warps of the pair
+  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const float2 u = FIRST ? x[e] : y[e];
+    const float2 v = FIRST ? y[e] : x[e];
+    al += u.x * u.x + u.y * u.y;
+    be += v.x * v.x + v.y * v.y;
+    gr += u.x * v.x + u.y * v.y;
+    gi += u.x * v.y - u.y * v.x;
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  gr = warp_sum(gr);
+  gi = warp_sum(gi);
+  const float gabs = sqrtf(gr * gr + gi * gi);
+  if (!ok || !(al > tiny) || !(be > tiny) || !(gabs > tiny)) return;
+  const float rel = gabs / sqrtf(al * be);
+  if (!(rel > tol)) return;
+  if (FIRST) {
+    local_off = fmaxf(local_off, rel);
+    if ((threadIdx.x & 31) == 0) ++rot;
+  }
+  const float er = gr / gabs, ei = -gi / gabs;
+  const float zeta = (al - be) / (2.f * gabs);
+  const float sg = zeta >= 0.f ? 1.f : -1.f;
+  const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + t * t);
+  const float sn = c * t;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const float2 u = FIRST ? x[e] : y[e];
+    const float2 v = FIRST ? y[e] : x[e];
+    const float2 ve{v.x * er - v.y * ei, v.x * ei + v.y * er};
+    x[e] = FIRST ? float2{c * u.x - sn * ve.x, c * u.y - sn * ve.y}
+                 : float2{sn * u.x + c * ve.x, sn * u.y + c * ve.y};
+  }
+}
+
+template <int SUB, int E>
+__device__ __forceinline__ void wp4_subround(float2 (&x)[E], bool valid_me, const bool* valid_all, float2* sbuf,
+                                             int m, int& buf, float tiny, float tol, float& local_off,
+                                             unsigned long long& rot) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = wp4_partner<SUB>(w);
+  float2* base = sbuf + (long long)buf * 8 * m;
+  float2* mine = base + (long long)w * m;
+  const float2* theirs = base + (long long)p * m;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane + 32 * e;
+    if (i < m) mine[i] = x[e];
+  }
+  __syncthreads();
+  float2 y[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane + 32 * e;
+    y[e] = (i < m) ? theirs[i] : float2{0.f, 0.f};
+  }
+  buf ^= 1;   // the next sub-round writes the other buffer: no second barrier
+  const bool ok = valid_me && valid_all[p];
+  if (w < p) wp4_pair<true, E>(x, y, ok, tiny, tol, local_off, rot);
+  else wp4_pair<false, E>(x, y, ok, tiny, tol, local_off, rot);
+}
+
+template <int E>
+__global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__ G, int m, int n, int nblk,
+                                                            float tol, int max_sweeps,
+                                                            const double* __restrict__ fro2, float zero_rel,
+                                                            JacobiCtl* ctl) {
+  extern __shared__ float2 sbuf[];          // 2 buffers x 8 columns x m
+  __shared__ bool valid_all[8];
+  __shared__ float off_w[8];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const unsigned nb = gridDim.x;
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const float tiny = (float)fmax(fz, 1e-30);
+  const float conv = fmaxf(tol, 2e-4f);   // stop when a sweep's largest rotation is below conv
+  int sweep = 0, buf = 0;
+  unsigned long long rot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < nblk - 1; ++r) {
+      for (int pb = blockIdx.x; pb < nblk / 2; pb += gridDim.x) {
+        int I, J;
+        round_robin_pair(r, pb, nblk, I, J);
+        const int col = (w < 4 ? I : J) * 4 + (w & 3);
+        const bool valid = col < n;
+        if (lane == 0) valid_all[w] = valid;
+        float2 x[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = (valid && i < m) ? G[(long long)col * m + i] : float2{0.f, 0.f};
+        }
+        if (r == 0) {
+          wp4_subround<0, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+          wp4_subround<1, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+          wp4_subround<2, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        }
+        wp4_subround<3, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<4, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<5, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<6, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        if (valid) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            if (i < m) G[(long long)col * m + i] = x[e];
+          }
+        }
+        __syncthreads();   // valid_all and the buffers are reused by the next pair of blocks
+      }
+      if (lane == 0) off_w[w] = local_off;
+      __syncthreads();
+      if (tid == 0) {
+        float mx = 0.f;
+        for (int i = 0; i < 8; ++i) mx = fmaxf(mx, off_w[i]);
+        if (mx > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(mx));
+      }
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) {
+        if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+        return;
+      }
+      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > conv)) { ++sweep; break; }
+  }
+  if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > conv && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
 // ---- column norms, sort, truncation rank
 
 template <typename R>
@@ -449,9 +791,12 @@ __global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const 
     // never kept: the cut is the larger of rel_cut * s_1 and that level
     const double zthr = zero_rel * sqrt(*fro2);              // on the column norm
     const double scut = fmax(rel_cut * s1, squared ? sqrt(zthr) : zthr);
-    int k = 0;
+    int k = 0, nnz = 0;
     double f = 0, tot = 0;
-    for (int i = 0; i < n; ++i) tot += v[i] * v[i];
+    for (int i = 0; i < n; ++i) {
+      tot += v[i] * v[i];
+      if (v[i] > (squared ? sqrt(zthr) : zthr)) ++nnz;
+    }
     for (int i = 0; i < n && k < chi; ++i) {
       if (v[i] > scut) ++k; else break;
     }
@@ -473,6 +818,7 @@ __global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const 
     res->n = n;
     res->f = f;
     res->norm2 = tot;
+    res->nnz = nnz;
   }
 }
 
@@ -515,9 +861,22 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   void* fn;
   int threads = 128, blocks;
-  const bool blocked = sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
+  const bool wide = sizeof(R) == 4 && m <= 32 * 32 && n >= 16;
+  const bool blocked = !wide && sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
   int nblk = 0;
-  if (blocked) {
+  size_t dyn_smem = 0;
+  if (wide) {
+    threads = 256;
+    nblk = (n + 3) / 4;
+    nblk += nblk & 1;
+    if (m <= 32 * 8) fn = (void*)jacobi_wp4_kernel<8>;
+    else if (m <= 32 * 16) fn = (void*)jacobi_wp4_kernel<16>;
+    else fn = (void*)jacobi_wp4_kernel<32>;
+    dyn_smem = (size_t)2 * 8 * m * sizeof(float2);
+    cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    if (ea != cudaSuccess) return ea;
+    blocks = nblk / 2;
+  } else if (blocked) {
     nblk = (n + 3) / 4;
     nblk += nblk & 1;
     if (m <= 128 * 2) fn = (void*)jacobi_blk_kernel<2>;
@@ -534,16 +893,16 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
     fn = (void*)jacobi_kernel<R>;
     blocks = (pairs + threads / 32 - 1) / (threads / 32);
   }
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn_smem);
   if (e != cudaSuccess) return e;
   const int cap = sms * per_sm;   // every CTA of a cooperative launch must be resident
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   C2* g = reinterpret_cast<C2*>(G);
   R tl = (R)tol, zr = (R)zero_rel;
-  int mm = m, nn = n, npp = blocked ? nblk : np, ms = max_sweeps;
+  int mm = m, nn = n, npp = (wide || blocked) ? nblk : np, ms = max_sweeps;
   void* args[] = {&g, &mm, &nn, &npp, &tl, &ms, (void*)&fro2, &zr, &c};
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, st);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, dyn_smem, st);
 }
 
 }  // namespace
