@@ -265,7 +265,18 @@ def main(argv=None):
     ap.add_argument("--chi", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="random", choices=["random", "qaoa"],
+                    help="qaoa: grid-graph QAOA (p = --layers), reports the sampled cut value")
+    ap.add_argument("--layers", type=int, default=4, help="QAOA levels")
+    ap.add_argument("--samples", type=int, default=10000)
+    ap.add_argument("--chi-oracle", type=int, default=64)
+    ap.add_argument("--fidelity-report", action="store_true",
+                    help="report F_tilde of every precision on the 24-qubit version and the oracle")
     args = ap.parse_args(argv)
+    if args.fidelity_report:
+        return fidelity_report(args)
+    if args.workload == "qaoa":
+        return qaoa_report(args)
     world, rank, local = dist_setup()
     workload = f"random circuit {args.rows}x{args.cols} ({args.rows * args.cols}q), K=2 cycles/step, chi={args.chi}, 2 sweeps"
     config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
@@ -358,6 +369,79 @@ def main(argv=None):
         "state": {"max_chi": r["max_chi"], "max_D": r["max_D"]},
     }
     print(json.dumps(line))
+    return 0
+
+
+def fidelity_report(args):
+    """Config-2 error table: the 4x6 (24-qubit) version of the random circuit,
+    10 steps, every precision of the library against its FP64 run, and at a
+    bond dimension the CPU oracle finishes in minutes, against the oracle."""
+    import math
+    from paper_2207_05612_gb300 import Context
+    from synthetic import circuits as sc
+    rows, cols = 4, 6
+    circ = sc.random_circuit(rows, cols, 20, seed=args.seed)
+    out = {"report": "fidelity", "workload": "random circuit 4x6 (24q), 20 cycles, K=2, 2 sweeps"}
+    for chi in (512, args.chi_oracle):
+        res = {}
+        for name in ("fp64", "fp32", "tf32x3", "bf16x3"):
+            ctx = Context(rows, cols, chi, precision=PRECISIONS[name])
+            t0 = time.perf_counter()
+            for layer in circ.layers:
+                ctx.apply_layer(layer)
+                ctx.sweep(2)
+            lf, _ = ctx.fidelity()
+            res[name] = {"log_F_tilde": lf, "seconds": time.perf_counter() - t0}
+            ctx.close()
+        for name in res:
+            res[name]["rel_err_vs_fp64"] = abs(res[name]["log_F_tilde"] - res["fp64"]["log_F_tilde"])
+        if chi == args.chi_oracle:
+            from oracle import dmrg as od
+            from oracle import mpo as om
+            order = om.snake_order(rows, cols)
+            t0 = time.perf_counter()
+            mps = od.product_state(rows * cols)
+            lo = 0.0
+            for layer in circ.layers:
+                mps, r = od.compress_layer(mps, om.layer_mpo(layer, order, compress=False), chi)
+                lo += math.log(r.f_delta)
+            res["oracle"] = {"log_F_tilde": lo, "seconds": time.perf_counter() - t0}
+            for name in ("fp64", "fp32", "tf32x3", "bf16x3"):
+                res[name]["rel_err_vs_oracle"] = abs(res[name]["log_F_tilde"] - lo)
+        out[f"chi={chi}"] = res
+    print(json.dumps(out))
+    return 0
+
+
+def qaoa_report(args):
+    """Config 3: QAOA MaxCut on the rows x cols grid graph, p levels, from
+    |+>^N, chi = --chi, precision --precision (TF32x3 by default in the
+    configuration); samples --samples bit strings and reports the mean cut."""
+    import torch
+    from paper_2207_05612_gb300 import Context
+    from synthetic import circuits as sc
+    circ, gam, bet, edges = sc.qaoa_circuit(args.rows, args.cols, args.layers, seed=args.seed)
+    n = args.rows * args.cols
+    ctx = Context(args.rows, args.cols, args.chi, precision=PRECISIONS[args.precision], timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for layer in circ.layers:
+        ctx.apply_layer(layer)
+        ctx.sweep(2)
+    t1 = time.perf_counter()
+    bits = ctx.sample(args.samples, seed=args.seed + 1)
+    t2 = time.perf_counter()
+    e = np.array(edges)
+    cut = np.sum(bits[:, e[:, 0]] != bits[:, e[:, 1]], axis=1).astype(float)
+    lf, fd = ctx.fidelity()
+    st = ctx.stats()
+    print(json.dumps({"report": "qaoa", "grid": f"{args.rows}x{args.cols}", "p": args.layers, "chi": args.chi,
+                      "precision": args.precision, "edges": len(edges),
+                      "updates_per_s": st["updates"] / max(t1 - t0, 1e-9), "sweep_seconds": t1 - t0,
+                      "samples": args.samples, "sample_seconds": t2 - t1,
+                      "cut_mean": float(cut.mean()), "cut_stderr": float(cut.std(ddof=1) / np.sqrt(len(cut))),
+                      "log_F_tilde": lf, "eps_tilde": float(1 - np.exp(lf / max(1, len(edges) * args.layers))),
+                      "gammas": [float(g) for g in gam], "betas": [float(b) for b in bet]}))
     return 0
 
 

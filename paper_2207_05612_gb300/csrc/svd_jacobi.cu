@@ -591,17 +591,20 @@ __device__ __forceinline__ int wp4_partner(int w) {
 template <bool FIRST, int E>
 __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], bool ok, float tiny, float tol,
                                          float& local_off, unsigned long long& rot) {
-  // (u, v) = (first, second) column: the same arithmetic in both warps of the pair
-  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+  // (u, v) = (first, second) column: the same arithmetic in both warps of the
+  // pair.  Packed FP32x2 FMAs: nu = (sum ux^2, sum uy^2), nv likewise,
+  // p1 = (sum ux vx, sum uy vy), p2 = (sum ux vy, sum uy vx).
+  float2 nu{0.f, 0.f}, nv{0.f, 0.f}, p1{0.f, 0.f}, p2{0.f, 0.f};
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const float2 u = FIRST ? x[e] : y[e];
     const float2 v = FIRST ? y[e] : x[e];
-    al += u.x * u.x + u.y * u.y;
-    be += v.x * v.x + v.y * v.y;
-    gr += u.x * v.x + u.y * v.y;
-    gi += u.x * v.y - u.y * v.x;
+    nu = __ffma2_rn(u, u, nu);
+    nv = __ffma2_rn(v, v, nv);
+    p1 = __ffma2_rn(u, v, p1);
+    p2 = __ffma2_rn(u, make_float2(v.y, v.x), p2);
   }
+  float al = nu.x + nu.y, be = nv.x + nv.y, gr = p1.x + p1.y, gi = p2.x - p2.y;
   al = warp_sum(al);
   be = warp_sum(be);
   gr = warp_sum(gr);
@@ -620,13 +623,16 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
   const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float c = 1.f / sqrtf(1.f + t * t);
   const float sn = c * t;
+  const float2 E2{er, er}, EI{-ei, ei};
+  const float2 CC{c, c}, SS{sn, sn}, NS{-sn, -sn};
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const float2 u = FIRST ? x[e] : y[e];
     const float2 v = FIRST ? y[e] : x[e];
-    const float2 ve{v.x * er - v.y * ei, v.x * ei + v.y * er};
-    x[e] = FIRST ? float2{c * u.x - sn * ve.x, c * u.y - sn * ve.y}
-                 : float2{sn * u.x + c * ve.x, sn * u.y + c * ve.y};
+    // ve = v e^{-i phi} = (vx er - vy ei, vy er + vx ei)
+    const float2 ve = __ffma2_rn(make_float2(v.y, v.x), EI, __fmul2_rn(v, E2));
+    // first: c u - s ve ; second: s u + c ve
+    x[e] = FIRST ? __ffma2_rn(CC, u, __fmul2_rn(NS, ve)) : __ffma2_rn(SS, u, __fmul2_rn(CC, ve));
   }
 }
 

@@ -238,3 +238,26 @@ def test_tensor_core_exact_regime(prec):
     bits = all_bitstrings(12)
     tol = 2e-4 if prec == 1 else 2e-5
     assert np.abs(ctx.amplitude(bits) - sv.amplitudes(exact, bits)).max() < tol
+
+
+@pytest.mark.parametrize("prec,chi", [(0, 64), (2, 64), (2, 10)])
+def test_qaoa_sampled_cut_value(prec, chi):
+    """Config-3 read-out on a small grid: the mean cut value of 20000 samples
+    agrees (4 sigma) with <C> = sum_edges (1 - <Z_i Z_j>)/2 of the simulated
+    state; at chi = 2^{N/2} that state is the exact one."""
+    circ, g, b, edges = sc.qaoa_circuit(3, 4, 3, seed=5)
+    ctx, per = gpu_run(circ, chi, precision=prec)
+    if chi == 64:
+        psi = sv.run(12, circ.layers)[-1]
+    else:
+        mps, _ = ctx.get_mps()
+        from oracle import mpo as om
+        psi = od.mps_dense(mps, om.snake_order(3, 4))
+    p = (np.abs(psi) ** 2)
+    p = p / p.sum()
+    idx = np.indices([2] * 12)
+    exp_c = sum(float(np.sum(p * (idx[u] != idx[v]))) for (u, v) in edges)
+    smp = ctx.sample(20000, seed=9)
+    e = np.array(edges)
+    cut = np.sum(smp[:, e[:, 0]] != smp[:, e[:, 1]], axis=1)
+    assert abs(cut.mean() - exp_c) < 4 * cut.std() / np.sqrt(len(cut)) + 1e-9
