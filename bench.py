@@ -265,8 +265,12 @@ def main(argv=None):
     ap.add_argument("--chi", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="random", choices=["random", "qaoa"],
-                    help="qaoa: grid-graph QAOA (p = --layers), reports the sampled cut value")
+    ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch"],
+                    help="qaoa: grid-graph QAOA (p = --layers), reports the sampled cut value; "
+                         "batch: independent instances of uneven N, depth and chi on concurrent streams")
+    ap.add_argument("--batch-count", type=int, default=32, help="batch: number of instances")
+    ap.add_argument("--workers", default="auto",
+                    help="batch: worker streams, or 'auto' to pick the best of 1, 2, 4, 8, 16 on a calibration subset")
     ap.add_argument("--layers", type=int, default=4, help="QAOA levels")
     ap.add_argument("--samples", type=int, default=10000)
     ap.add_argument("--chi-oracle", type=int, default=64)
@@ -277,6 +281,8 @@ def main(argv=None):
         return fidelity_report(args)
     if args.workload == "qaoa":
         return qaoa_report(args)
+    if args.workload == "batch":
+        return batch_report(args)
     world, rank, local = dist_setup()
     workload = f"random circuit {args.rows}x{args.cols} ({args.rows * args.cols}q), K=2 cycles/step, chi={args.chi}, 2 sweeps"
     config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
@@ -381,7 +387,10 @@ def fidelity_report(args):
     from synthetic import circuits as sc
     rows, cols = 4, 6
     circ = sc.random_circuit(rows, cols, 20, seed=args.seed)
-    out = {"report": "fidelity", "workload": "random circuit 4x6 (24q), 20 cycles, K=2, 2 sweeps"}
+    out = {"report": "fidelity", "workload": "random circuit 4x6 (24q), 20 cycles, K=2, 2 sweeps",
+           "note": "rel_err = |delta log F_tilde| = relative error of F_tilde; "
+                   "fp64_gates_perturbed_1e-7 gives the spread of the method itself under a "
+                   "rounding-sized change of its input"}
     for chi in (512, args.chi_oracle):
         res = {}
         for name in ("fp64", "fp32", "tf32x3", "bf16x3"):
@@ -393,6 +402,17 @@ def fidelity_report(args):
             lf, _ = ctx.fidelity()
             res[name] = {"log_F_tilde": lf, "seconds": time.perf_counter() - t0}
             ctx.close()
+        # the method's own sensitivity: FP64 on the circuit with every gate
+        # perturbed by a unitary of size 1e-7 (about one complex64 rounding)
+        pc = sc.perturb_circuit(circ, 1e-7, seed=args.seed + 1)
+        ctx = Context(rows, cols, chi, precision=PRECISIONS["fp64"])
+        t0 = time.perf_counter()
+        for layer in pc.layers:
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+        lf, _ = ctx.fidelity()
+        ctx.close()
+        res["fp64_gates_perturbed_1e-7"] = {"log_F_tilde": lf, "seconds": time.perf_counter() - t0}
         for name in res:
             res[name]["rel_err_vs_fp64"] = abs(res[name]["log_F_tilde"] - res["fp64"]["log_F_tilde"])
         if chi == args.chi_oracle:
@@ -442,6 +462,59 @@ def qaoa_report(args):
                       "cut_mean": float(cut.mean()), "cut_stderr": float(cut.std(ddof=1) / np.sqrt(len(cut))),
                       "log_F_tilde": lf, "eps_tilde": float(1 - np.exp(lf / max(1, len(edges) * args.layers))),
                       "gammas": [float(g) for g in gam], "betas": [float(b) for b in bet]}))
+    return 0
+
+
+def batch_report(args):
+    """Batched workload: --batch-count independent random-circuit instances,
+    N uniform in {16, 20, 24, 30, 36, 42, 54} (near-rectangular grids), depth
+    uniform in 8..20 cycles, chi uniform in {32, 64, 128, 256}, K = 2, two
+    sweeps per step.  The worker count is tuned on a calibration subset; the
+    whole batch then runs on the tuned count and on one worker (the instances
+    one at a time), and the aggregate updates/s of both are reported."""
+    from paper_2207_05612_gb300 import binding
+    from synthetic import circuits as sc
+    prec = PRECISIONS[args.precision]
+    insts = sc.batch_instances(args.batch_count, seed=args.seed)
+    opt = binding.dmrgc_default_options()
+    opt.precision = prec
+
+    def run(subset, workers):
+        items, keep = binding.pack_batch([(b.rows, b.cols, b.chi, b.circuit.layers, 2) for b in subset])
+        wall = binding.dmrgc_batch_run(items, len(subset), workers, opt)
+        res = [items[i] for i in range(len(subset))]
+        bad = [(i, r.status) for i, r in enumerate(res) if r.status != 0]
+        if bad:
+            raise RuntimeError(f"batch instances failed: {bad[:5]}")
+        ups = sum(r.updates for r in res)
+        return wall, ups, res
+
+    run(insts[:2], 2)   # warm-up: module load, tensor-map encoder, kernel attributes
+    tune = {}
+    if args.workers == "auto":
+        calib = insts[:min(len(insts), 12)]
+        for w in (1, 2, 4, 8, 16):
+            wall, ups, _ = run(calib, w)
+            tune[w] = ups / wall
+        workers = max(tune, key=tune.get)
+    else:
+        workers = int(args.workers)
+    wall_b, ups_b, res_b = run(insts, workers)
+    wall_s, ups_s, res_s = run(insts, 1)
+    dlog = max(abs(a.log_F_tilde - b.log_F_tilde) for a, b in zip(res_b, res_s))
+    print(json.dumps({
+        "report": "batch", "precision": args.precision, "instances": len(insts),
+        "workload": "random circuits, N in {16,20,24,30,36,42,54}, 8-20 cycles, chi in {32,64,128,256}, "
+                    "K=2, 2 sweeps per step",
+        "mix": {"n": [b.rows * b.cols for b in insts], "cycles": [b.cycles for b in insts],
+                "chi": [b.chi for b in insts]},
+        "updates": ups_b,
+        "workers": workers, "autotune_updates_per_s": {str(k): v for k, v in tune.items()},
+        "batched_updates_per_s": ups_b / wall_b, "batched_seconds": wall_b,
+        "serial_updates_per_s": ups_s / wall_s, "serial_seconds": wall_s,
+        "speedup": wall_s / wall_b,
+        "max_abs_dlog_F_tilde_batched_vs_serial": dlog,
+        "log_F_tilde": [r.log_F_tilde for r in res_b]}))
     return 0
 
 

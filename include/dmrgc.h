@@ -180,6 +180,32 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out);
 
+/* Batched open-mode runs of independent circuits (the compression step of
+ * Sec. IV.B applied layer after layer, Sec. IV.C) on one GPU.  n_workers host
+ * threads each own a CUDA stream and one context that is re-initialised for
+ * every instance it takes from the shared queue (its device buffers are kept,
+ * so allocation stops once a worker has seen its largest instance); instances
+ * of different size and bond dimension run concurrently on the streams.
+ * Options (precision, cutoffs) apply to all; options.cuda_stream is ignored.
+ * For each item the caller fills the inputs; the call fills the outputs. */
+typedef struct {
+  int rows, cols;            /* grid of this instance (n_qubits = rows*cols) */
+  dmrgc_grid grid_view;      /* must equal {rows, cols, 0} */
+  int chi;                   /* bond dimension */
+  int n_layers;              /* compression steps */
+  int n_sweeps;              /* dmrgc_sweep argument per step (2 = n_s of the paper's schedule) */
+  const dmrgc_gate* gates;   /* all layers' gates, concatenated in order (host) */
+  const int* layer_sizes;    /* n_layers gate counts (host) */
+  double log_F_tilde;        /* out: Eq. (Ftilde-sup) */
+  double seconds;            /* out: wall time of this instance */
+  long long updates;         /* out: two-site updates done */
+  int status;                /* out: dmrgc_status of this instance */
+  int worker;                /* out: worker that ran it */
+} dmrgc_batch_item;
+
+dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, const dmrgc_options* opt,
+                             double* wall_seconds);
+
 /* Truncated SVD of a device matrix that allocates no memory at all.
  *
  * The paper has no counterpart: this is a service for callers that cannot

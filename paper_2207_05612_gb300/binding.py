@@ -15,6 +15,7 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libdmrgc.so")
 
 DMRGC_FP64, DMRGC_BF16X3, DMRGC_TF32X3, DMRGC_FP32 = 0, 1, 2, 3
+DMRGC_OK, DMRGC_EINVAL, DMRGC_ENOMEM, DMRGC_ECUDA, DMRGC_ENOCONV, DMRGC_ENUMERIC, DMRGC_ETIMEOUT, DMRGC_ESTATE = range(8)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENUMERIC",
           6: "ETIMEOUT", 7: "ESTATE"}
 
@@ -45,6 +46,14 @@ class Stats(C.Structure):
                 ("svd_ms", C.c_double), ("svd_flops", C.c_double), ("svd_launches", C.c_longlong),
                 ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
                 ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("grid_view", Grid), ("chi", C.c_int),
+                ("n_layers", C.c_int), ("n_sweeps", C.c_int), ("gates", C.POINTER(Gate)),
+                ("layer_sizes", C.POINTER(C.c_int)), ("log_F_tilde", C.c_double),
+                ("seconds", C.c_double), ("updates", C.c_longlong), ("status", C.c_int),
+                ("worker", C.c_int)]
 
 
 _lib = None
@@ -84,7 +93,8 @@ def lib():
                                      C.c_void_p, P(C.c_int), C.c_void_p]
         L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
-        for name in ("dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+        L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), P(C.c_double)]
+        for name in ("dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
             getattr(L, name).restype = C.c_int
@@ -236,6 +246,35 @@ def dmrgc_svd_noalloc(precision: int, g_ptr: int, m: int, n: int, chi: int, rel_
                                    C.c_void_p(s_ptr), C.byref(k), C.c_void_p(u_ptr),
                                    C.c_void_p(stream)))
     return k.value
+
+
+def pack_batch(instances):
+    """[(rows, cols, chi, layers, n_sweeps)] -> (array of dmrgc_batch_item, keep-alive list).
+    `layers` is a list of gate lists [(q0, q1, U)]."""
+    items = (BatchItem * max(len(instances), 1))()
+    keep = []
+    for i, (rows, cols, chi, layers, n_sweeps) in enumerate(instances):
+        flat = [g for layer in layers for g in layer]
+        gates = pack_gates(flat)
+        sizes = (C.c_int * max(len(layers), 1))(*[len(layer) for layer in layers])
+        keep += [gates, sizes]
+        it = items[i]
+        it.rows, it.cols, it.chi = rows, cols, chi
+        it.grid_view = Grid(rows, cols, 0)
+        it.n_layers, it.n_sweeps = len(layers), n_sweeps
+        it.gates = C.cast(gates, C.POINTER(Gate))
+        it.layer_sizes = C.cast(sizes, C.POINTER(C.c_int))
+        it.status = -1
+    return items, keep
+
+
+def dmrgc_batch_run(items, count: int, n_workers: int, options: Options | None = None) -> float:
+    """Runs `count` packed instances on `n_workers` streams; fills the items'
+    outputs and returns the wall time in seconds."""
+    wall = C.c_double()
+    opt = options if options is not None else dmrgc_default_options()
+    _check(lib().dmrgc_batch_run(items, count, n_workers, C.byref(opt), C.byref(wall)))
+    return wall.value
 
 
 class Context:

@@ -12,10 +12,13 @@
 // next right-to-left pass needs at the same bond, and Y_{i+1} likewise the
 // other way round, so each update computes one of X / Y and reuses the other.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -688,20 +691,28 @@ dmrgc_status dmrgc_default_options(dmrgc_options* opt) {
   return DMRGC_OK;
 }
 
-dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const dmrgc_options* opt,
-                          dmrgc_ctx** out) {
-  if (!out || !grid) return DMRGC_EINVAL;
-  *out = nullptr;
-  if (n_qubits < 1 || n_qubits > 4096 || grid->rows < 1 || grid->cols < 1 ||
-      grid->rows * grid->cols != n_qubits || grid->order != 0 || chi < 1 || chi > 4096)
-    return DMRGC_EINVAL;
-  dmrgc_ctx* c = new (std::nothrow) dmrgc_ctx();
-  if (!c) return DMRGC_ENOMEM;
-  if (opt) c->opt = *opt; else dmrgc_default_options(&c->opt);
-  if (c->opt.precision < 0 || c->opt.precision > 3 || c->opt.svd_mode != 0) { delete c; return DMRGC_EINVAL; }
+}  // extern "C"
+
+namespace {
+
+bool valid_shape(int n_qubits, const dmrgc_grid* grid, int chi) {
+  return grid && n_qubits >= 1 && n_qubits <= 4096 && grid->rows >= 1 && grid->cols >= 1 &&
+         grid->rows * grid->cols == n_qubits && grid->order == 0 && chi >= 1 && chi <= 4096;
+}
+
+// (Re)initialise a context for a new circuit in |0...0>.  Device buffers the
+// context already owns are kept (they only grow), so a context can be reused
+// for a sequence of circuits without new allocations once it has seen the
+// largest one.
+dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int chi, const dmrgc_options& opt) {
+  c->opt = opt;
+  if (c->opt.precision < 0 || c->opt.precision > 3 || c->opt.svd_mode != 0)
+    return fail(c, DMRGC_EINVAL, "bad options");
   c->N = n_qubits; c->chi = chi; c->rows = grid->rows; c->cols = grid->cols; c->m = n_qubits / 2;
   c->st = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
-  c->fp64 = c->opt.precision == DMRGC_FP64;
+  const bool fp64 = c->opt.precision == DMRGC_FP64;
+  // buffers are sized in bytes, so a change of element size needs no release
+  c->fp64 = fp64;
   c->esz = c->fp64 ? 16 : 8;
   // numerically-zero level of a Jacobi column, relative to |theta|_F, and the
   // cutoffs above it: FP64 1e-13 / sweep 1e-12 / zip 1e-5; complex64 1e-5 / 2e-5 / 4e-3
@@ -711,6 +722,7 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
   c->sweep_cut = c->opt.sweep_rel_cutoff > 0 ? c->opt.sweep_rel_cutoff : (c->fp64 ? 1e-12 : 2e-5);
   c->zip_cut = c->opt.zip_rel_cutoff > 0 ? c->opt.zip_rel_cutoff : (c->fp64 ? 1e-5 : 4e-3);
   c->max_jsweeps = c->opt.max_jacobi_sweeps > 0 ? c->opt.max_jacobi_sweeps : 40;
+  c->order.clear();
   for (int col = 0; col < c->cols; ++col)
     for (int k = 0; k < c->rows; ++k) {
       const int r = (col % 2 == 0) ? k : c->rows - 1 - k;
@@ -718,27 +730,119 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
     }
   c->site_of.assign(n_qubits, 0);
   for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
-  c->A.resize(n_qubits); c->B.resize(n_qubits); c->Wx.resize(n_qubits); c->Wy.resize(n_qubits);
-  c->XY.resize(n_qubits); c->E.resize(n_qubits); c->xyk.assign(n_qubits, 0);
-  c->warm.resize(n_qubits); c->warm_dim.assign(n_qubits, 0); c->warm_side.assign(n_qubits, 0);
+  for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E, &c->warm})
+    if ((int)v->size() < n_qubits) v->resize(n_qubits);
+  c->xyk.assign(n_qubits, 0);
+  c->warm_dim.assign(n_qubits, 0); c->warm_side.assign(n_qubits, 0);
   c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);
-  dmrgc_status s = ensure(c, c->one, 64);
-  if (s == DMRGC_OK) {
-    cudaError_t e = set_scalar_one(c->one.p, c->fp64, c->st);
-    for (int i = 0; i < n_qubits && e == cudaSuccess && s == DMRGC_OK; ++i) {
-      s = ensure(c, c->B[i], 2 * c->esz);
-      if (s == DMRGC_OK) {
-        e = cudaMemsetAsync(c->B[i].p, 0, 2 * c->esz, c->st);
-        if (e == cudaSuccess) e = set_scalar_one(c->B[i].p, c->fp64, c->st);
-      }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    if (e != cudaSuccess) s = fail(c, DMRGC_ECUDA, cudaGetErrorString(e));
+  c->L = EnvRef(); c->R = EnvRef();
+  c->phase = 0; c->bond = 0; c->dir = -1; c->centre = 0;
+  c->log_ft = 0.0; c->f_cur = 1.0;
+  c->hist.clear();
+  c->err.clear();
+  TRY(ensure(c, c->one, 64));
+  CK(set_scalar_one(c->one.p, c->fp64, c->st));
+  for (int i = 0; i < n_qubits; ++i) {
+    TRY(ensure(c, c->B[i], 2 * c->esz));
+    CK(cudaMemsetAsync(c->B[i].p, 0, 2 * c->esz, c->st));
+    CK(set_scalar_one(c->B[i].p, c->fp64, c->st));
   }
+  if (c->tcerr.p) CK(cudaMemsetAsync(c->tcerr.p, 0, 64, c->st));
+  return sync(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const dmrgc_options* opt,
+                          dmrgc_ctx** out) {
+  if (!out || !grid) return DMRGC_EINVAL;
+  *out = nullptr;
+  if (!valid_shape(n_qubits, grid, chi)) return DMRGC_EINVAL;
+  dmrgc_ctx* c = new (std::nothrow) dmrgc_ctx();
+  if (!c) return DMRGC_ENOMEM;
+  dmrgc_options o;
+  if (opt) o = *opt; else dmrgc_default_options(&o);
+  c->esz = 0;
+  dmrgc_status s = ctx_setup(c, n_qubits, grid, chi, o);
   if (s != DMRGC_OK) { delete c; return s; }
-  c->phase = 0;
-  c->centre = 0;
   *out = c;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, const dmrgc_options* opt,
+                             double* wall_seconds) {
+  if (wall_seconds) *wall_seconds = 0.0;
+  if (count < 0 || (count > 0 && !items) || n_workers < 1 || n_workers > 64) return DMRGC_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    dmrgc_batch_item& it = items[i];
+    if (!valid_shape(it.rows * it.cols, &it.grid_view, it.chi) || it.grid_view.rows != it.rows ||
+        it.grid_view.cols != it.cols ||
+        it.n_layers < 0 || (it.n_layers > 0 && (!it.gates || !it.layer_sizes)) || it.n_sweeps < 0)
+      return DMRGC_EINVAL;
+    for (int l = 0; l < it.n_layers; ++l)
+      if (it.layer_sizes[l] < 0) return DMRGC_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    items[i].status = DMRGC_ESTATE;   // not run (yet)
+    items[i].worker = -1;
+    items[i].log_F_tilde = 0.0;
+    items[i].seconds = 0.0;
+    items[i].updates = 0;
+  }
+  dmrgc_options base;
+  if (opt) base = *opt; else dmrgc_default_options(&base);
+  if (base.precision < 0 || base.precision > 3 || base.svd_mode != 0) return DMRGC_EINVAL;
+  if (count == 0) return DMRGC_OK;
+  if (n_workers > count) n_workers = count;
+  std::atomic<int> next{0};
+  std::vector<dmrgc_status> worker_status(n_workers, DMRGC_OK);
+  const auto t0 = std::chrono::steady_clock::now();
+  auto work = [&](int wid) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      worker_status[wid] = DMRGC_ECUDA;
+      return;
+    }
+    dmrgc_ctx* c = new (std::nothrow) dmrgc_ctx();
+    if (!c) { worker_status[wid] = DMRGC_ENOMEM; cudaStreamDestroy(st); return; }
+    c->esz = 0;
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      dmrgc_batch_item& it = items[i];
+      const auto s0 = std::chrono::steady_clock::now();
+      dmrgc_options o = base;
+      o.cuda_stream = st;
+      o.timing = 0;
+      dmrgc_status s = ctx_setup(c, it.rows * it.cols, &it.grid_view, it.chi, o);
+      const dmrgc_gate* g = it.gates;
+      long long updates0 = c->stats.updates;
+      for (int l = 0; l < it.n_layers && s == DMRGC_OK; ++l) {
+        s = dmrgc_apply_layer(c, g, it.layer_sizes[l]);
+        g += it.layer_sizes[l];
+        if (s == DMRGC_OK) s = dmrgc_sweep(c, it.n_sweeps, nullptr);
+      }
+      double lf = 0.0;
+      if (s == DMRGC_OK) s = dmrgc_fidelity(c, &lf, nullptr);
+      it.status = (int)s;
+      it.log_F_tilde = lf;
+      it.updates = c->stats.updates - updates0;
+      it.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - s0).count();
+      it.worker = wid;
+    }
+    delete c;
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < n_workers; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+  if (wall_seconds)
+    *wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (auto st : worker_status)
+    if (st != DMRGC_OK) return st;
   return DMRGC_OK;
 }
 

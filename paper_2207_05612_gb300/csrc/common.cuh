@@ -126,6 +126,12 @@ cudaError_t build_site_mpo(const int* plan_tab, SitePlan sp, const GateDev* gate
 
 // ------------------------------------------------------------------- misc
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// (minus its static shared memory), once per kernel and thread-safely, so that
+// host threads launching the same kernel with different sizes on different
+// streams never lower the limit under one another.
+cudaError_t allow_dyn_smem(const void* fn);
+
 cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void* dst, bool fp64,
                            cudaStream_t st);   // dst[c*rows + r] = op(src[r*cols + c])
 cudaError_t copy_conj(const void* src, long long n, void* dst, bool fp64, cudaStream_t st);

@@ -429,14 +429,10 @@ bool make_map(CUtensorMap* tm, int esz, void* base, int kp, int rows, int inst, 
 }
 
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
 }
 
 template <int ESZ>
@@ -507,12 +503,7 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st) 
     zero_c_kernel<<<zg, 256, 0, st>>>((float2*)g.C, g.M, g.N, g.ldc, g.sC1, g.sC2, g.b2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  static bool attr_set[5] = {false, false, false, false, false};
-  if (!attr_set[ESZ]) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set[ESZ] = true;
-  }
+  if ((e = allow_dyn_smem((const void*)tc_gemm_kernel<ESZ>)) != cudaSuccess) return e;
   dim3 grid((2 * g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM, (unsigned)(g.b1 * g.b2 * split));
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   tc_gemm_kernel<ESZ><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(tAh, tAl, tBh, tBl, a);

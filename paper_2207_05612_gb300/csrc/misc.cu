@@ -2,6 +2,9 @@
 // physical-index-first permutation of MPS tensors, identities, norms, scaling.
 #include "common.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace dmrgc {
 namespace {
 
@@ -108,6 +111,25 @@ __global__ void from_z_kernel(const double2* __restrict__ x, long long n, C2* __
 }
 
 }  // namespace
+
+cudaError_t allow_dyn_smem(const void* fn) {
+  static std::mutex mu;
+  static std::vector<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first == dev && d.second == fn) return cudaSuccess;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+  done.emplace_back(dev, fn);
+  return cudaSuccess;
+}
 
 cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* dst, cudaStream_t st) {
   if (fp64) from_z_kernel<<<blocks_for(n), 256, 0, st>>>(src, n, (double2*)dst);

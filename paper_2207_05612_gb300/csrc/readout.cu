@@ -141,11 +141,11 @@ cudaError_t amplitudes(const void* const* sites, const int* bonds, const int* or
   const int threads = max_bond >= 256 ? 256 : 128;
   cudaError_t e;
   if (fp64) {
-    e = cudaFuncSetAttribute(amp_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dyn_smem((const void*)amp_kernel<double2>);
     if (e != cudaSuccess) return e;
     amp_kernel<double2><<<(unsigned)count, threads, sm, st>>>(sites, bonds, order, n_sites, bits, count, out);
   } else {
-    e = cudaFuncSetAttribute(amp_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dyn_smem((const void*)amp_kernel<float2>);
     if (e != cudaSuccess) return e;
     amp_kernel<float2><<<(unsigned)count, threads, sm, st>>>(sites, bonds, order, n_sites, bits, count, out);
   }
@@ -162,12 +162,12 @@ cudaError_t sample_bits(const void* const* sites, const void* const* emat, const
   const int threads = 256;
   cudaError_t e;
   if (fp64) {
-    e = cudaFuncSetAttribute(sample_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dyn_smem((const void*)sample_kernel<double2>);
     if (e != cudaSuccess) return e;
     sample_kernel<double2><<<(unsigned)count, threads, sm, st>>>(sites, emat, bonds, order, n_sites,
                                                                  centre, seed, count, out);
   } else {
-    e = cudaFuncSetAttribute(sample_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dyn_smem((const void*)sample_kernel<float2>);
     if (e != cudaSuccess) return e;
     sample_kernel<float2><<<(unsigned)count, threads, sm, st>>>(sites, emat, bonds, order, n_sites,
                                                                 centre, seed, count, out);

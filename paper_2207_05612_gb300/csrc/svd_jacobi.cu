@@ -879,7 +879,7 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
     else if (m <= 32 * 16) fn = (void*)jacobi_wp4_kernel<16>;
     else fn = (void*)jacobi_wp4_kernel<32>;
     dyn_smem = (size_t)2 * 8 * m * sizeof(float2);
-    cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    cudaError_t ea = allow_dyn_smem(fn);
     if (ea != cudaSuccess) return ea;
     blocks = nblk / 2;
   } else if (blocked) {

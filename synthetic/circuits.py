@@ -182,3 +182,55 @@ def gates_to_records(layer) -> np.ndarray:
         buf[1:2 * flat.size:2] = flat.imag
         rec[i]["mat"] = buf
     return rec
+
+
+# Batched workload: independent random-circuit instances of uneven size, depth
+# and bond dimension.  Grid for each qubit count: the nearest near-rectangular one.
+BATCH_GRIDS = {16: (4, 4), 20: (4, 5), 24: (4, 6), 30: (5, 6), 36: (6, 6), 42: (6, 7), 54: (6, 9)}
+BATCH_CHIS = (32, 64, 128, 256)
+
+
+@dataclass
+class BatchInstance:
+    rows: int
+    cols: int
+    cycles: int
+    chi: int
+    seed: int
+    circuit: Circuit
+
+
+def batch_instances(count: int, seed: int = 0, qubits=tuple(BATCH_GRIDS), chis=BATCH_CHIS,
+                    min_cycles: int = 8, max_cycles: int = 20) -> list[BatchInstance]:
+    """`count` instances: N uniform over `qubits`, depth uniform in
+    [min_cycles, max_cycles] cycles, chi uniform over `chis`; each instance's
+    gates drawn from its own seed (Sequence I, K = 2 cycles per layer)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(qubits))
+        rows, cols = BATCH_GRIDS[n]
+        cycles = int(rng.integers(min_cycles, max_cycles + 1))
+        chi = int(rng.choice(chis))
+        s = int(rng.integers(2**31))
+        out.append(BatchInstance(rows, cols, cycles, chi, s, random_circuit(rows, cols, cycles, seed=s)))
+    return out
+
+
+def perturb_circuit(circ: Circuit, eps: float, seed: int = 0) -> Circuit:
+    """The same circuit with every gate U replaced by exp(i eps H) U, H a
+    random Hermitian matrix with unit-variance entries: a unitary perturbation
+    of size ~eps, used to measure how sensitive a result is to rounding-level
+    changes of its input."""
+    rng = np.random.default_rng(seed)
+    out = Circuit(circ.rows, circ.cols)
+    out.n_two_qubit = circ.n_two_qubit
+    for layer in circ.layers:
+        new = []
+        for (a, b, u) in layer:
+            h = rng.normal(size=u.shape) + 1j * rng.normal(size=u.shape)
+            h = (h + h.conj().T) / 2
+            w, v = np.linalg.eigh(h)
+            new.append((a, b, (v * np.exp(1j * eps * w)) @ v.conj().T @ u))
+        out.layers.append(new)
+    return out

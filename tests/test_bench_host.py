@@ -59,3 +59,15 @@ def test_clock_parser_and_peaks():
     assert r["reasons"] == ["sw_power_cap"]
     assert abs(bench.alu_peak_tflops(False, 2070.0) - 152 * 128 * 2 * 2.07e-3) < 1e-9
     assert bench.alu_peak_tflops(True, 2070.0) == 1.25
+
+
+def test_batch_generator_mix():
+    import math
+    from synthetic import circuits as sc
+    insts = sc.batch_instances(64, seed=0)
+    ns = {b.rows * b.cols for b in insts}
+    assert ns <= set(sc.BATCH_GRIDS) and len(ns) >= 5
+    assert all(8 <= b.cycles <= 20 and b.chi in sc.BATCH_CHIS for b in insts)
+    assert all(len(b.circuit.layers) == math.ceil(b.cycles / 2) for b in insts)
+    again = sc.batch_instances(64, seed=0)
+    assert [(b.rows, b.cycles, b.chi, b.seed) for b in insts] == [(b.rows, b.cycles, b.chi, b.seed) for b in again]

@@ -1,0 +1,65 @@
+"""Batched runs (independent instances of uneven N, depth and chi on
+concurrent worker streams) against one-context runs and the oracle."""
+import pytest
+
+from synthetic import circuits as sc
+from tests.helpers import gpu_run, layer_gaps, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+# (rows, cols, chi, cycles, seed): exact (chi >= 2^(N/2)) and truncating cases
+CASES = [(2, 3, 8, 6, 1), (3, 4, 64, 8, 2), (3, 4, 16, 8, 3), (2, 4, 4, 6, 4),
+         (3, 3, 8, 8, 5), (4, 4, 32, 8, 6), (2, 5, 8, 7, 7), (4, 5, 32, 6, 8)]
+
+
+def _batch(cases, workers, precision=0):
+    from paper_2207_05612_gb300 import binding
+    circs = [sc.random_circuit(r, c, cyc, seed=s) for (r, c, chi, cyc, s) in cases]
+    items, keep = binding.pack_batch([(r, c, chi, circ.layers, 2)
+                                      for (r, c, chi, _, _), circ in zip(cases, circs)])
+    opt = binding.dmrgc_default_options()
+    opt.precision = precision
+    wall = binding.dmrgc_batch_run(items, len(cases), workers, opt)
+    return circs, [items[i] for i in range(len(cases))], wall
+
+
+def test_batch_matches_single_context_and_oracle():
+    circs, res, wall = _batch(CASES, workers=3)
+    assert wall > 0
+    for (rows, cols, chi, cyc, seed), circ, r in zip(CASES, circs, res):
+        n = rows * cols
+        assert r.status == 0
+        assert r.updates == len(circ.layers) * 2 * 2 * (n - 1)
+        assert 0 <= r.worker < 3
+        ctx, per = gpu_run(circ, chi, precision=0)
+        assert abs(r.log_F_tilde - per[-1]["log_ft"]) < 1e-12
+        ctx.close()
+        if chi >= 2 ** (n // 2):
+            assert abs(r.log_F_tilde) < 1e-10
+        _, _, results, lo = oracle_run(circ, chi)
+        if all(g > 1e-8 for g in layer_gaps(results)) and not any(x.zip_ambiguous for x in results):
+            assert abs(r.log_F_tilde - lo) < 1e-10, (rows, cols, chi)
+    # more than one worker took part
+    assert len({r.worker for r in res}) > 1
+
+
+def test_batch_is_independent_of_worker_count():
+    _, one, _ = _batch(CASES, workers=1)
+    _, many, _ = _batch(CASES, workers=8)
+    for a, b in zip(one, many):
+        assert a.status == 0 and b.status == 0
+        assert abs(a.log_F_tilde - b.log_F_tilde) < 1e-12
+        assert a.updates == b.updates
+
+
+def test_batch_mixed_precision_and_reuse_across_sizes():
+    """A worker reuses its context for instances that grow and shrink; the
+    complex64 tensor-core path gives the single-context result."""
+    cases = [(4, 6, 64, 8, 11), (2, 3, 4, 4, 12), (4, 6, 32, 8, 13), (3, 4, 64, 6, 14)]
+    circs, res, _ = _batch(cases, workers=1, precision=1)
+    for (rows, cols, chi, cyc, seed), circ, r in zip(cases, circs, res):
+        assert r.status == 0
+        ctx, per = gpu_run(circ, chi, precision=1)
+        ctx.close()
+        assert abs(r.log_F_tilde - per[-1]["log_ft"]) < 3e-4 * max(1.0, abs(per[-1]["log_ft"]))
+

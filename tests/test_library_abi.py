@@ -46,3 +46,34 @@ def test_pack_gates_roundtrip():
     m = np.array(arr[0].mat[:])
     assert np.allclose(m[0::2] + 1j * m[1::2], u.reshape(-1))
     assert arr[1].q1 == -1
+
+
+def test_batch_item_layout_and_host_validation():
+    """dmrgc_batch_run validates every item on the host before any CUDA call."""
+    from paper_2207_05612_gb300 import binding
+    from synthetic import circuits as sc
+    assert ctypes.sizeof(binding.BatchItem) == 80
+    lib = binding.lib()
+    wall = ctypes.c_double(-1.0)
+    opt = binding.dmrgc_default_options()
+    assert lib.dmrgc_batch_run(None, 0, 1, ctypes.byref(opt), ctypes.byref(wall)) == 0
+    assert wall.value == 0.0
+    circ = sc.random_circuit(2, 3, 2, seed=0)
+    items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2), (2, 3, 4, circ.layers, 2)])
+    bad = [
+        ("n_workers", lambda it: None, 0),
+        ("chi", lambda it: setattr(it, "chi", 0), 1),
+        ("grid", lambda it: setattr(it, "grid_view", binding.Grid(3, 2, 0)), 1),
+        ("order", lambda it: setattr(it, "grid_view", binding.Grid(2, 3, 1)), 1),
+        ("sweeps", lambda it: setattr(it, "n_sweeps", -1), 1),
+        ("gates", lambda it: setattr(it, "gates", None), 1),
+    ]
+    for name, mutate, workers in bad:
+        items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2), (2, 3, 4, circ.layers, 2)])
+        mutate(items[1])
+        st = lib.dmrgc_batch_run(items, 2, workers, ctypes.byref(opt), ctypes.byref(wall))
+        assert st == binding.DMRGC_EINVAL, name
+        assert items[0].status == -1        # nothing ran, outputs untouched
+    opt.precision = 7
+    items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2)])
+    assert lib.dmrgc_batch_run(items, 1, 1, ctypes.byref(opt), ctypes.byref(wall)) == binding.DMRGC_EINVAL
