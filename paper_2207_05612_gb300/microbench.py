@@ -1,0 +1,107 @@
+"""Kernel micro-benchmarks through the C ABI, one kernel class at a time, on
+seeded random inputs.  Also the small-case driver for profiler captures of a
+single kernel.
+
+  python -m paper_2207_05612_gb300.microbench gemm --precision bf16x3 --m 65536 --n 1024 --k 512
+  python -m paper_2207_05612_gb300.microbench svd --precision fp32 --m 1024 --n 1024
+
+gemm: C = A B through dmrgc_test_gemm (host complex128 buffers in and out, so
+the wall time includes the transfers and the operand split); reports the wall
+time per call and the algorithmic complex flops 8 M N K.
+svd: the one-sided Jacobi, truncation and gather on a device matrix through
+dmrgc_svd_noalloc, timed with CUDA events on its stream; the matrix is
+re-copied from a pristine device copy before each call (the copy is outside
+the events).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import binding
+
+PREC = {"fp64": binding.DMRGC_FP64, "bf16x3": binding.DMRGC_BF16X3,
+        "tf32x3": binding.DMRGC_TF32X3, "fp32": binding.DMRGC_FP32}
+
+
+def _cplx(rng, shape):
+    return (rng.normal(size=shape) + 1j * rng.normal(size=shape)) / np.sqrt(2.0)
+
+
+def bench_gemm(prec: int, m: int, n: int, k: int, reps: int, seed: int) -> dict:
+    rng = np.random.default_rng(seed)
+    a = _cplx(rng, (m, k))
+    b = _cplx(rng, (k, n))
+    binding.dmrgc_test_gemm(prec, a, b, 0, 0, m, n, k)   # warm-up
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        c = binding.dmrgc_test_gemm(prec, a, b, 0, 0, m, n, k)
+    dt = (time.perf_counter() - t0) / reps
+    rows = rng.choice(m, size=min(m, 64), replace=False)
+    ref = a[rows] @ b
+    err = float(np.abs(c[rows] - ref).max() / np.abs(ref).max())
+    return {"kernel": "gemm", "m": m, "n": n, "k": k, "wall_ms_per_call": dt * 1e3,
+            "algorithmic_gflop": 8.0 * m * n * k / 1e9, "max_rel_err_sampled_rows": err,
+            "note": "wall time includes host<->device copies and operand split"}
+
+
+def bench_svd(prec: int, m: int, n: int, reps: int, seed: int) -> dict:
+    import torch
+    rng = np.random.default_rng(seed)
+    g = _cplx(rng, (m, n)) / np.sqrt(m * n)
+    cdt = torch.complex128 if prec == binding.DMRGC_FP64 else torch.complex64
+    dev = torch.device("cuda")
+    # column-major m x n = row-major n x m transposed
+    pristine = torch.from_numpy(np.ascontiguousarray(g.T)).to(cdt).to(dev)
+    work = torch.empty_like(pristine)
+    s = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(m * n, dtype=cdt, device=dev)
+    st = torch.cuda.current_stream()
+    chi = n
+
+    def call():
+        return binding.dmrgc_svd_noalloc(prec, work.data_ptr(), m, n, chi, 1e-12, s.data_ptr(),
+                                         u.data_ptr(), st.cuda_stream)
+
+    work.copy_(pristine)
+    call()   # warm-up (and the first-call set-up)
+    times = []
+    for _ in range(reps):
+        work.copy_(pristine)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        call()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ref = np.linalg.svd(g, compute_uv=False)
+    err = float(np.abs(s.cpu().numpy() - ref).max() / ref[0])
+    return {"kernel": "svd", "m": m, "n": n, "ms_per_call": float(np.median(times)),
+            "max_rel_err_s": err}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("kernel", choices=["gemm", "svd"])
+    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--m", type=int, default=1024)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--k", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    prec = PREC[a.precision]
+    if a.kernel == "gemm":
+        out = bench_gemm(prec, a.m, a.n, a.k, a.reps, a.seed)
+    else:
+        out = bench_svd(prec, a.m, a.n, a.reps, a.seed)
+    out["precision"] = a.precision
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
