@@ -265,7 +265,9 @@ def main(argv=None):
     ap.add_argument("--chi", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch"],
+    ap.add_argument("--records", type=int, default=20000, help="learned: training records to log")
+    ap.add_argument("--eval-layers", type=int, default=4, help="learned: layers of the random circuit to run")
+    ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned"],
                     help="qaoa: grid-graph QAOA (p = --layers), reports the sampled cut value; "
                          "batch: independent instances of uneven N, depth and chi on concurrent streams")
     ap.add_argument("--batch-count", type=int, default=32, help="batch: number of instances")
@@ -283,6 +285,8 @@ def main(argv=None):
         return qaoa_report(args)
     if args.workload == "batch":
         return batch_report(args)
+    if args.workload == "learned":
+        return learned_report(args)
     world, rank, local = dist_setup()
     workload = f"random circuit {args.rows}x{args.cols} ({args.rows * args.cols}q), K=2 cycles/step, chi={args.chi}, 2 sweeps"
     config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
@@ -462,6 +466,84 @@ def qaoa_report(args):
                       "cut_mean": float(cut.mean()), "cut_stderr": float(cut.std(ddof=1) / np.sqrt(len(cut))),
                       "log_F_tilde": lf, "eps_tilde": float(1 - np.exp(lf / max(1, len(edges) * args.layers))),
                       "gammas": [float(g) for g in gam], "betas": [float(b) for b in bet]}))
+    return 0
+
+
+def learned_report(args):
+    """Learned truncated SVD.  (1) Log rank-model records with the full Jacobi
+    SVD on small random and QAOA circuits (4x6, 6x9; chi 64-128) until
+    --records; (2) train the model on the GPU; (3) run the same workloads with
+    svd_mode 0 (Jacobi), 1 (sketch rank = bond dimension) and 2 (learned):
+    QAOA 6x9 p=4 at chi=256 (the structured configuration) and the first
+    --eval-layers layers of the 6x9 random circuit at --chi (1024 in the
+    learned configuration), each against the Jacobi run."""
+    import torch
+    from paper_2207_05612_gb300 import Context, binding
+    from synthetic import circuits as sc
+    prec = PRECISIONS[args.precision]
+    t0 = time.perf_counter()
+    xs, ys, n, seed = [], [], 0, 0
+    sources = {}
+    while n < args.records and time.perf_counter() - t0 < 600:
+        if seed % 3 == 2:
+            circ, _, _, _ = sc.qaoa_circuit(6, 9, 4, seed=1000 + seed)
+            chi, name = 64, "qaoa 6x9 chi=64"
+        else:
+            circ = sc.random_circuit(4, 6, 20, seed=1000 + seed)
+            chi, name = (64 if seed % 3 == 0 else 128), "random 4x6 chi=64/128"
+        ctx = Context(circ.rows, circ.cols, chi, precision=prec, log_rank_records=1)
+        for layer in circ.layers:
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+        x, y = ctx.rank_records()
+        ctx.close()
+        xs.append(x)
+        ys.append(y)
+        n += len(y)
+        sources[name] = sources.get(name, 0) + len(y)
+        seed += 1
+    x = np.concatenate(xs)
+    y = np.concatenate(ys)
+    t_log = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    params, loss = binding.dmrgc_mlp_train(x, y, epochs=40, batch=256, lr=2e-3, seed=args.seed)
+    t_train = time.perf_counter() - t1
+
+    def run(circ, chi, mode, layers):
+        ctx = Context(circ.rows, circ.cols, chi, precision=prec, timing=True, svd_mode=mode)
+        if mode == 2:
+            ctx.set_rank_model(params)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        for layer in circ.layers[:layers]:
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - ts
+        lf, _ = ctx.fidelity()
+        st = ctx.stats()
+        ctx.close()
+        return {"updates_per_s": st["updates"] / dt, "seconds": dt, "log_F_tilde": lf,
+                "svd_ms": st["svd_ms"], "gemm_ms": st["gemm_ms"], "jacobi_sweeps": st["jacobi_sweeps"],
+                "sketches_accepted": st["rsvd_accepted"], "sketches_tried": st["rsvd_attempts"]}
+
+    out = {"report": "learned", "precision": args.precision,
+           "training": {"records": int(len(y)), "sources": sources, "log_seconds": t_log,
+                        "train_seconds": t_train, "epochs": 40, "loss_first": float(loss[0]),
+                        "loss_last": float(loss[-1]), "label": "log2 r, r = rank holding 1-1e-6 of the kept weight"}}
+    qc, _, _, _ = sc.qaoa_circuit(6, 9, 4, seed=args.seed + 7)
+    rc = sc.random_circuit(6, 9, 20, seed=args.seed)
+    for name, circ, chi, layers in (("qaoa 6x9 p=4 chi=256", qc, 256, len(qc.layers)),
+                                    (f"random 6x9 chi={args.chi} first {args.eval_layers} layers", rc, args.chi,
+                                     args.eval_layers)):
+        res = {}
+        for mode, label in ((0, "jacobi"), (1, "sketch_rank_rule"), (2, "learned")):
+            res[label] = run(circ, chi, mode, layers)
+        for label in res:
+            res[label]["speedup_vs_jacobi"] = res["jacobi"]["seconds"] / res[label]["seconds"]
+            res[label]["abs_dlog_F_tilde_vs_jacobi"] = abs(res[label]["log_F_tilde"] - res["jacobi"]["log_F_tilde"])
+        out[name] = res
+    print(json.dumps(out))
     return 0
 
 

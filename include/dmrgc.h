@@ -62,7 +62,13 @@ typedef struct {
 
 typedef struct {
   int precision;              /* DMRGC_FP64 ... DMRGC_FP32 */
-  int svd_mode;               /* 0 = one-sided Jacobi (only mode) */
+  int svd_mode;               /* truncated SVD of theta in the sweep:
+                                 0 = one-sided Jacobi;
+                                 1 = randomized range finder with a sketch of r + p columns,
+                                     r = the bond's current dimension, falling back to the
+                                     Jacobi SVD when the sketch fails its acceptance test;
+                                 2 = the same with r predicted by the rank model
+                                     (dmrgc_set_rank_model) */
   double sweep_rel_cutoff;    /* keep s_mu > cutoff * s_1 in the sweep SVD; <= 0: default
                                  (1e-12 for FP64, 2e-5 for the complex64 modes) */
   double zip_rel_cutoff;      /* same for the truncating steps of the zip-up guess; <= 0:
@@ -71,6 +77,16 @@ typedef struct {
   unsigned long long seed;    /* reserved */
   void* cuda_stream;          /* cudaStream_t to launch on; NULL = default stream */
   int timing;                 /* 1: record CUDA-event time per kernel class (dmrgc_stats) */
+  int rsvd_oversample;        /* p, extra sketch columns; <= 0: 8 */
+  int rsvd_power_iters;       /* q, power iterations (each re-orthonormalised); 0..8
+                                 (dmrgc_default_options: 1) */
+  double rsvd_tolerance;      /* tol of the sketch acceptance: accept when the weight of theta
+                                 outside the sketch is <= tol * f (the result is then within
+                                 tol of the optimal update), or, at a bond already updated in
+                                 this layer, when f >= (1 - tol) * the current partial
+                                 fidelity; <= 0: 1e-6 for FP64, 2e-5 for complex64 */
+  int log_rank_records;       /* 1: log one rank-model record per full (Jacobi) SVD at a bond
+                                 updated before (dmrgc_rank_records) */
 } dmrgc_options;
 
 typedef struct {
@@ -94,6 +110,8 @@ typedef struct {
   double other_ms;              /* permutes, copies, norms */
   long long updates;            /* two-site updates done */
   long long kernel_launches;    /* every kernel the library launched */
+  long long rsvd_attempts;      /* randomized SVDs tried (svd_mode 1, 2) */
+  long long rsvd_accepted;      /* of which accepted (the rest fell back to Jacobi) */
 } dmrgc_stats;
 
 /* Fill *opt with defaults (FP64, Jacobi, default cutoffs, default stream). */
@@ -180,13 +198,61 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out);
 
+/* ---- Rank model (svd_mode 2)
+ *
+ * Not in the paper: a multilayer perceptron that predicts, for the next update
+ * at a bond, r = the smallest rank whose leading singular values hold all but
+ * 1e-6 of the weight the update keeps (its log2).  The randomized SVD then
+ * sketches r + p columns; the acceptance test above judges the result.
+ *
+ * Input (DMRGC_MLP_IN floats): 32 samples of log10(s_mu^2 / sum_{nu<k} s_nu^2)
+ * at mu_j = round(j (k-1) / 31), j = 0..31, of the spectrum the last update at
+ * the bond kept (k values); log2 k; log2 of the layer MPO's bond dimension at
+ * the bond (the operator rank of the gates crossing it); log2 of the smaller
+ * side of theta; 1 if the bond was already updated in this layer, else 0.
+ * Network: x -> relu(W1 x + b1) -> relu(W2 h + b2) -> w3 . h + b3, hidden width
+ * DMRGC_MLP_HIDDEN.  Parameters, FP32, in this order: W1 [H][IN] row-major,
+ * b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1] (DMRGC_MLP_PARAMS floats). */
+#define DMRGC_MLP_IN 36
+#define DMRGC_MLP_HIDDEN 128
+#define DMRGC_MLP_PARAMS (DMRGC_MLP_HIDDEN * DMRGC_MLP_IN + DMRGC_MLP_HIDDEN + \
+                          DMRGC_MLP_HIDDEN * DMRGC_MLP_HIDDEN + DMRGC_MLP_HIDDEN + DMRGC_MLP_HIDDEN + 1)
+
+/* Load a rank model into the context (host FP32 parameters, copied; inference
+ * runs with BF16 weights and FP32 accumulation). */
+dmrgc_status dmrgc_set_rank_model(dmrgc_ctx* ctx, const float* params);
+
+/* Move the records logged since the last call (options.log_rank_records) to
+ * the caller: features [count][DMRGC_MLP_IN], labels [count] (log2 r judged by
+ * the full Jacobi SVD).  At most max records are returned; *count is set. */
+dmrgc_status dmrgc_rank_records(dmrgc_ctx* ctx, float* features, float* labels, int max, int* count);
+
+/* Train a rank model on the GPU (hand-written FP32 kernels): mean squared error
+ * on the labels, Adam (beta 0.9, 0.999), mini-batches of `batch` rows drawn
+ * without replacement per epoch from a SplitMix64-seeded shuffle; inputs and
+ * labels are standardised internally and the returned parameters act on raw
+ * inputs.  x: host [n][DMRGC_MLP_IN], y: host [n]; params_out: host
+ * DMRGC_MLP_PARAMS floats; epoch_loss (optional): host [epochs], the mean
+ * standardised loss of each epoch. */
+dmrgc_status dmrgc_mlp_train(const float* x, const float* y, int n, int epochs, int batch, float lr,
+                             unsigned long long seed, float* params_out, float* epoch_loss);
+
+/* Loss (1/n) sum (f(x) - y)^2 and its gradient with respect to every
+ * parameter, in the parameter order above, FP32 on the GPU (host buffers). */
+dmrgc_status dmrgc_mlp_loss_grad(const float* params, const float* x, const float* y, int n, float* loss,
+                                 float* grad);
+
+/* y_out[n] = f(x) on the GPU; bf16 = 1 uses the BF16 inference kernel. */
+dmrgc_status dmrgc_mlp_predict(const float* params, const float* x, int n, int bf16, float* y_out);
+
 /* Batched open-mode runs of independent circuits (the compression step of
  * Sec. IV.B applied layer after layer, Sec. IV.C) on one GPU.  n_workers host
  * threads each own a CUDA stream and one context that is re-initialised for
  * every instance it takes from the shared queue (its device buffers are kept,
  * so allocation stops once a worker has seen its largest instance); instances
  * of different size and bond dimension run concurrently on the streams.
- * Options (precision, cutoffs) apply to all; options.cuda_stream is ignored.
+ * Options (precision, cutoffs) apply to all; options.cuda_stream is ignored;
+ * svd_mode 2 (which needs a rank model per context) returns DMRGC_EINVAL.
  * For each item the caller fills the inputs; the call fills the outputs. */
 typedef struct {
   int rows, cols;            /* grid of this instance (n_qubits = rows*cols) */

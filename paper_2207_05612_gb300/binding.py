@@ -34,7 +34,9 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("svd_mode", C.c_int),
                 ("sweep_rel_cutoff", C.c_double), ("zip_rel_cutoff", C.c_double),
                 ("max_jacobi_sweeps", C.c_int), ("seed", C.c_ulonglong),
-                ("cuda_stream", C.c_void_p), ("timing", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("timing", C.c_int),
+                ("rsvd_oversample", C.c_int), ("rsvd_power_iters", C.c_int),
+                ("rsvd_tolerance", C.c_double), ("log_rank_records", C.c_int)]
 
 
 class Gate(C.Structure):
@@ -45,7 +47,8 @@ class Stats(C.Structure):
     _fields_ = [("gemm_ms", C.c_double), ("gemm_flops", C.c_double), ("gemm_launches", C.c_longlong),
                 ("svd_ms", C.c_double), ("svd_flops", C.c_double), ("svd_launches", C.c_longlong),
                 ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
-                ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong)]
+                ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong),
+                ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong)]
 
 
 class BatchItem(C.Structure):
@@ -94,7 +97,14 @@ def lib():
         L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), P(C.c_double)]
-        for name in ("dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+        fp = C.c_void_p
+        L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
+        L.dmrgc_rank_records.argtypes = [C.c_void_p, fp, fp, C.c_int, P(C.c_int)]
+        L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
+        L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
+        L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
+        for name in ("dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+                     "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
             getattr(L, name).restype = C.c_int
@@ -277,6 +287,65 @@ def dmrgc_batch_run(items, count: int, n_workers: int, options: Options | None =
     return wall.value
 
 
+MLP_IN, MLP_HIDDEN = 36, 128
+MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def dmrgc_set_rank_model(ctx, params: np.ndarray) -> None:
+    p = _f32(params, (MLP_PARAMS,))
+    _check(lib().dmrgc_set_rank_model(ctx, p.ctypes.data), ctx)
+
+
+def dmrgc_rank_records(ctx, max_records: int = 1 << 20):
+    """Moves the logged (inputs [n][36], labels [n]) out of the context."""
+    cnt = C.c_int()
+    x = np.zeros((max_records, MLP_IN), dtype=np.float32)
+    y = np.zeros(max_records, dtype=np.float32)
+    _check(lib().dmrgc_rank_records(ctx, x.ctypes.data, y.ctypes.data, max_records, C.byref(cnt)), ctx)
+    return x[:cnt.value].copy(), y[:cnt.value].copy()
+
+
+def dmrgc_mlp_train(x: np.ndarray, y: np.ndarray, epochs: int, batch: int = 256, lr: float = 1e-3,
+                    seed: int = 0):
+    """Train the rank model on the GPU; returns (params, per-epoch loss)."""
+    x = _f32(x)
+    y = _f32(y)
+    n = y.size
+    assert x.shape == (n, MLP_IN)
+    params = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = np.zeros(epochs, dtype=np.float32)
+    _check(lib().dmrgc_mlp_train(x.ctypes.data, y.ctypes.data, n, epochs, batch, lr, seed,
+                                 params.ctypes.data, loss.ctypes.data))
+    return params, loss
+
+
+def dmrgc_mlp_loss_grad(params: np.ndarray, x: np.ndarray, y: np.ndarray):
+    p = _f32(params, (MLP_PARAMS,))
+    x = _f32(x)
+    y = _f32(y)
+    loss = C.c_float()
+    grad = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(lib().dmrgc_mlp_loss_grad(p.ctypes.data, x.ctypes.data, y.ctypes.data, y.size, C.byref(loss),
+                                     grad.ctypes.data))
+    return loss.value, grad
+
+
+def dmrgc_mlp_predict(params: np.ndarray, x: np.ndarray, bf16: bool = True) -> np.ndarray:
+    p = _f32(params, (MLP_PARAMS,))
+    x = _f32(x)
+    out = np.zeros(x.shape[0], dtype=np.float32)
+    _check(lib().dmrgc_mlp_predict(p.ctypes.data, x.ctypes.data, x.shape[0], 1 if bf16 else 0,
+                                   out.ctypes.data))
+    return out
+
+
 class Context:
     """Owning handle around the C context (marshalling only)."""
 
@@ -321,6 +390,12 @@ class Context:
 
     def reset_stats(self):
         dmrgc_reset_stats(self.h)
+
+    def set_rank_model(self, params):
+        dmrgc_set_rank_model(self.h, params)
+
+    def rank_records(self):
+        return dmrgc_rank_records(self.h)
 
     def close(self):
         if self.h:

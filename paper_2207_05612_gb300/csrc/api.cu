@@ -58,6 +58,17 @@ struct dmrgc_ctx {
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
   DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d, tcerr;
   TcWork tcw;
+  // randomized SVD and the rank model (svd_mode 1, 2)
+  DevBuf rs_om, rs_y, rs_q, rs_b, rs_h, rs_w, feat, mlp_w, mlp_out, lab;
+  int layer_no = 0;
+  std::vector<int> visit_layer;   // per bond: layer of the last update there (-1 none)
+  std::vector<int> rs_fail;       // per bond: layer in which a sketch was rejected
+  std::vector<int> kprev;         // per bond: kept rank at the last update (0 = none)
+  unsigned long long rs_ctr = 0;  // counter of the sketch random stream
+  double rs_tol = 1e-6;
+  int rs_p = 8, rs_pow = 1;
+  bool mlp_ready = false;
+  std::vector<float> rec_x, rec_y;   // logged (features, label) records
   EnvRef L, R;
   int phase = 0;           // 0 created, 1 guess ready / sweeping
   int bond = 0, dir = -1;  // next update (bond, bond+1), dir -1 = right-to-left
@@ -256,8 +267,13 @@ double jacobi_tol(const dmrgc_ctx* c, int m) {
 // Orthogonalise the columns of jw (m x n column-major), truncate; returns k, f.
 // squared: jw is a Gram matrix (its column norms are s^2); tie_rel > 0 applies
 // the multiplet rule at the cut.
+// W: the matrix (default jw); chi_cap: the most columns kept (default chi);
+// norm2 (optional): the sum of all s^2.
 dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, double tie_rel,
-                         int& k, double& f, int* nnz = nullptr) {
+                         int& k, double& f, int* nnz = nullptr, double* norm2 = nullptr,
+                         void* W = nullptr, int chi_cap = -1) {
+  if (!W) W = c->jw.p;
+  if (chi_cap < 0) chi_cap = c->chi;
   TRY(ensure(c, c->jctl, jacobi_ctl_bytes()));
   TRY(ensure(c, c->tres, trunc_bytes(n)));
   TRY(ensure(c, c->scal, 64));
@@ -265,10 +281,10 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   {
     Span sp(c, TC_SVD);
     int launches = 0;
-    CK(sum_abs2(c->jw.p, (long long)m * n, c->fp64, fro2, c->st));
-    CK(jacobi_orthogonalize(c->jw.p, m, n, c->fp64, jacobi_tol(c, m), c->max_jsweeps, fro2,
+    CK(sum_abs2(W, (long long)m * n, c->fp64, fro2, c->st));
+    CK(jacobi_orthogonalize(W, m, n, c->fp64, jacobi_tol(c, m), c->max_jsweeps, fro2,
                             c->zero_rel, c->jctl.p, c->st, &launches));
-    CK(truncate_columns(c->jw.p, m, n, c->fp64, c->chi, rel_cut, squared, tie_rel, fro2, c->zero_rel,
+    CK(truncate_columns(W, m, n, c->fp64, chi_cap, rel_cut, squared, tie_rel, fro2, c->zero_rel,
                         c->tres.p, c->st));
     c->stats.svd_launches += launches + 3;
     c->stats.kernel_launches += launches + 3;
@@ -288,6 +304,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   k = tr.k;
   f = tr.f;
   if (nnz) *nnz = tr.nnz;
+  if (norm2) *norm2 = tr.norm2;
   return DMRGC_OK;
 }
 
@@ -327,6 +344,225 @@ dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
   return gemm(c, g);
 }
 
+// ---- randomized truncated SVD (svd_mode 1, 2)
+//
+// Range finder of Halko, Martinsson and Tropp (SIAM Rev. 53, 2011): Y = G Omega
+// with a Gaussian Omega of l = r + p columns, q power iterations G (G^+ Q) with
+// re-orthonormalisation, B = Q^+ G, then the left singular vectors of B from the
+// eigenvectors of B B^+ (one-sided Jacobi on the Hermitian l x l matrix), and
+// U = Q W.  G = theta (left vectors, left-to-right update) or theta^+ (right
+// vectors, right-to-left update).  Every orthonormalisation is the one-sided
+// Jacobi with the numerical-zero level, so rank-deficient sketches lose their
+// null directions instead of dividing by them.
+//
+// Acceptance (else the update falls back to the full Jacobi SVD):
+//  - certificate: theta^+ theta = B^+ B + (rest), both positive semidefinite,
+//    so by Ky Fan the best weight of k <= chi singular values of theta is at
+//    most that of B plus |theta|^2 - |B|^2.  With f the weight kept from B:
+//    if k = chi the optimum is at most f + |theta|^2 - |B|^2; if fewer were
+//    kept (the rest fell below the cut) at most |theta|^2.  Accept when that
+//    excess is at most tol * f: the result is within tol of the optimal update;
+//  - or, at a bond already updated in this layer, f >= (1 - tol) f_cur: the
+//    update keeps the partial fidelity the sweep already reached.
+
+// orthonormal basis of the columns of W (column-major rows x cols): every
+// direction above the numerical-zero level, out row-major [rows][r]
+dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r) {
+  int k = 0, nnz = 0;
+  double f = 0;
+  TRY(svd_columns(c, rows, cols, 0.0, false, 0.0, k, f, &nnz, nullptr, W, cols));
+  r = k;
+  Span sp(c, TC_SVD);
+  CK(gather_columns(W, rows, cols, k, c->tres.p, false, 0, out, c->fp64, c->st));
+  c->stats.kernel_launches++;
+  return DMRGC_OK;
+}
+
+dmrgc_status rsvd_try(dmrgc_ctx* c, int i, bool adj, int mrow, int ncol, int l, bool& accepted, int& k,
+                      double& f) {
+  accepted = false;
+  const int mg = adj ? ncol : mrow, ng = adj ? mrow : ncol;
+  const size_t es = c->esz;
+  // op codes on theta (row-major [mrow][ncol]) giving G^T [ng][mg], conj(G) [mg][ng], G [mg][ng]
+  const int opGT = adj ? OP_R : OP_T;
+  const int opGc = adj ? OP_T : OP_R;
+  const int opG = adj ? OP_C : OP_N;
+  TRY(ensure(c, c->scal, 64));
+  double* fro_t = (double*)c->scal.p + 3;
+  TRY(ensure(c, c->rs_om, (size_t)ng * l * es));
+  TRY(ensure(c, c->rs_y, (size_t)l * std::max(mg, ng) * es));
+  TRY(ensure(c, c->rs_q, (size_t)mg * l * es));
+  {
+    Span sp(c, TC_SVD);
+    CK(sum_abs2(c->theta.p, (long long)mrow * ncol, c->fp64, fro_t, c->st));
+    CK(fill_gaussian(c->rs_om.p, (long long)ng * l, c->fp64, c->opt.seed, c->rs_ctr, c->st));
+    c->stats.kernel_launches += 2;
+  }
+  c->rs_ctr += 2ull * ng * l;
+  c->stats.rsvd_attempts++;
+  // Y^T = S^T G^T for a basis S [ng][cols]: [cols][mg] row-major = Y column-major
+  auto sketch = [&](const void* S, int cols) -> dmrgc_status {
+    GemmArgs g;
+    g.M = cols; g.N = mg; g.K = ng;
+    g.A = S; g.lda = cols; g.opA = OP_T;
+    g.B = c->theta.p; g.ldb = ncol; g.opB = opGT;
+    g.C = c->rs_y.p; g.ldc = mg;
+    return gemm(c, g);
+  };
+  TRY(sketch(c->rs_om.p, l));
+  int lq = 0;
+  TRY(orth_columns(c, c->rs_y.p, mg, l, c->rs_q.p, lq));
+  for (int it = 0; it < c->rs_pow; ++it) {
+    GemmArgs g;   // Z^T = Q^T conj(G): [lq][ng] = (G^+ Q) column-major
+    g.M = lq; g.N = ng; g.K = mg;
+    g.A = c->rs_q.p; g.lda = lq; g.opA = OP_T;
+    g.B = c->theta.p; g.ldb = ncol; g.opB = opGc;
+    g.C = c->rs_y.p; g.ldc = ng;
+    TRY(gemm(c, g));
+    int lz = 0;
+    TRY(orth_columns(c, c->rs_y.p, ng, lq, c->rs_om.p, lz));   // [ng][lz], in Omega's buffer
+    TRY(sketch(c->rs_om.p, lz));
+    TRY(orth_columns(c, c->rs_y.p, mg, lz, c->rs_q.p, lq));
+  }
+  TRY(ensure(c, c->rs_b, (size_t)lq * ng * es));
+  {
+    GemmArgs g;   // B = Q^+ G [lq][ng]
+    g.M = lq; g.N = ng; g.K = mg;
+    g.A = c->rs_q.p; g.lda = lq; g.opA = OP_C;
+    g.B = c->theta.p; g.ldb = ncol; g.opB = opG;
+    g.C = c->rs_b.p; g.ldc = ng;
+    TRY(gemm(c, g));
+  }
+  TRY(ensure(c, c->rs_h, (size_t)lq * lq * es));
+  {
+    GemmArgs g;   // H = B B^+ [lq][lq]; Hermitian, so the buffer is conj(H) column-major
+    g.M = lq; g.N = lq; g.K = ng;
+    g.A = c->rs_b.p; g.lda = ng; g.opA = OP_N;
+    g.B = c->rs_b.p; g.ldb = ng; g.opB = OP_C;
+    g.C = c->rs_h.p; g.ldc = lq;
+    TRY(gemm(c, g));
+  }
+  int kk = 0, nnz = 0;
+  double ff = 0, trh = 0, fro_theta = 0;
+  TRY(svd_columns(c, lq, lq, c->sweep_cut, true, 0.0, kk, ff, &nnz, &trh, c->rs_h.p, c->chi));
+  CK(cudaMemcpy(&fro_theta, fro_t, sizeof(double), cudaMemcpyDeviceToHost));
+  // weight the optimum could hold beyond ff: everything outside the sketch, and,
+  // when fewer than chi values were kept, the sketch's own values below the cut
+  const double tol = c->rs_tol;
+  const double gap = (fro_theta - trh) + (kk < c->chi ? trh - ff : 0.0);
+  const bool cert = gap <= tol * ff;
+  const bool keeps = c->visit_layer[i] == c->layer_no && ff >= (1.0 - tol) * c->f_cur;
+  if (!(cert || keeps)) {
+    c->rs_fail[i] = c->layer_no;
+    return DMRGC_OK;
+  }
+  accepted = true;
+  c->stats.rsvd_accepted++;
+  TRY(ensure(c, c->rs_w, (size_t)lq * kk * es));
+  {
+    Span sp(c, TC_SVD);   // normalised eigenvectors of conj(H): conj(W) [lq][kk]
+    CK(gather_columns(c->rs_h.p, lq, lq, kk, c->tres.p, true, 0, c->rs_w.p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  GemmArgs g;
+  if (!adj) {   // A_i = Q W [mrow][kk]
+    TRY(ensure(c, c->A[i], (size_t)mrow * kk * es));
+    g.M = mg; g.N = kk; g.K = lq;
+    g.A = c->rs_q.p; g.lda = lq; g.opA = OP_N;
+    g.B = c->rs_w.p; g.ldb = kk; g.opB = OP_R;
+    g.C = c->A[i].p; g.ldc = kk;
+  } else {      // A_{i+1} = (Q W)^+ [kk][ncol]
+    TRY(ensure(c, c->A[i + 1], (size_t)kk * ncol * es));
+    g.M = kk; g.N = mg; g.K = lq;
+    g.A = c->rs_w.p; g.lda = kk; g.opA = OP_T;
+    g.B = c->rs_q.p; g.ldb = lq; g.opB = OP_C;
+    g.C = c->A[i + 1].p; g.ldc = mg;
+  }
+  TRY(gemm(c, g));
+  k = kk;
+  f = ff;
+  return DMRGC_OK;
+}
+
+// Rank-model input at bond i: the summary of the spectrum at its last update
+// (32 values on the device), then log2 of that kept rank, log2 of the MPO bond
+// dimension there, log2 of the smaller side of theta, and 1 if the bond was
+// already updated in this layer.
+void model_extras(const dmrgc_ctx* c, int i, int nmin, float* e) {
+  e[0] = (float)std::log2((double)std::max(c->kprev[i], 1));
+  e[1] = (float)std::log2((double)std::max(c->D[i + 1], 1));
+  e[2] = (float)std::log2((double)std::max(nmin, 1));
+  e[3] = c->visit_layer[i] == c->layer_no ? 1.f : 0.f;
+}
+
+// Sketch size for the update at bond i, 0 = full Jacobi.
+dmrgc_status sketch_size(dmrgc_ctx* c, int i, int mrow, int ncol, int& l) {
+  l = 0;
+  const int nmin = std::min(mrow, ncol);
+  if (c->opt.svd_mode == 0 || nmin < 32) return DMRGC_OK;
+  int r = 0;
+  if (c->opt.svd_mode == 1) {
+    if (c->rs_fail[i] == c->layer_no) return DMRGC_OK;   // rejected here in this layer already
+    r = c->chiA[i + 1];                                   // the current bond dimension
+  } else {
+    if (!c->mlp_ready || c->kprev[i] <= 0) return DMRGC_OK;
+    float e[4];
+    model_extras(c, i, nmin, e);
+    TRY(ensure(c, c->mlp_out, 64));
+    {
+      Span sp(c, TC_SVD);
+      CK(mlp_infer_one(c->mlp_w.p, (const float*)c->feat.p + 32 * (size_t)i, e, (float*)c->mlp_out.p, c->st));
+      c->stats.kernel_launches++;
+    }
+    float y = 0.f;
+    CK(cudaMemcpyAsync(&y, c->mlp_out.p, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    TRY(sync(c));
+    if (!std::isfinite(y)) return DMRGC_OK;
+    r = (int)std::ceil(std::exp2(std::min(std::max((double)y, 0.0), 20.0)));
+  }
+  const int want = r + c->rs_p;
+  if (want >= (int)(0.7 * nmin)) return DMRGC_OK;
+  l = std::max(want, 1);
+  return DMRGC_OK;
+}
+
+// Before an update at bond i: the host copy of the rank-model input the record
+// logged by this update will carry.
+dmrgc_status record_begin(dmrgc_ctx* c, int i, int nmin, std::vector<float>& x) {
+  x.clear();
+  if (!c->opt.log_rank_records || c->kprev[i] <= 0) return DMRGC_OK;
+  x.resize(DMRGC_MLP_IN);
+  CK(cudaMemcpyAsync(x.data(), (const float*)c->feat.p + 32 * (size_t)i, 32 * sizeof(float),
+                     cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  model_extras(c, i, nmin, x.data() + 32);
+  return DMRGC_OK;
+}
+
+// After the SVD of an update at bond i with k kept (tres holds its spectrum):
+// the spectrum summary for the next visit and, for a full SVD, the record's label.
+dmrgc_status record_end(dmrgc_ctx* c, int i, int k, bool full, const std::vector<float>& x) {
+  if (c->opt.svd_mode == 2 || c->opt.log_rank_records) {
+    TRY(ensure(c, c->feat, sizeof(float) * 32 * (size_t)c->N));
+    Span sp(c, TC_SVD);
+    CK(spectrum_summary(c->tres.p, k, (float*)c->feat.p + 32 * (size_t)i, c->st));
+    c->stats.kernel_launches++;
+  }
+  if (full && !x.empty()) {
+    TRY(ensure(c, c->lab, 64));
+    CK(rank_label(c->tres.p, k, 1.0 - 1e-6, (int*)c->lab.p, c->st));
+    c->stats.kernel_launches++;
+    int r = 0;
+    CK(cudaMemcpyAsync(&r, c->lab.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    TRY(sync(c));
+    c->rec_x.insert(c->rec_x.end(), x.begin(), x.end());
+    c->rec_y.push_back((float)std::log2((double)std::max(r, 1)));
+  }
+  c->kprev[i] = k;
+  c->visit_layer[i] = c->layer_no;
+  return DMRGC_OK;
+}
+
 dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   // X_i from the running left environment
   EnvRef L = c->L;
@@ -336,29 +572,38 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   if (c->xyk[i + 1] != 'Y') return fail(c, DMRGC_ESTATE, "right cache missing");
   int mrow, ncol;
   TRY(form_theta(c, i, mrow, ncol));
-  TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-  if (c->warm_dim[i] == ncol && c->warm_side[i] == 'R') {
-    GemmArgs g;   // jw (column-major) = theta V_prev: row-major [ncol][mrow] = V^T theta^T
-    g.M = ncol; g.N = mrow; g.K = ncol;
-    g.A = c->warm[i].p; g.lda = ncol; g.opA = OP_N;
-    g.B = c->theta.p; g.ldb = ncol; g.opB = OP_T;
-    g.C = c->jw.p; g.ldc = mrow;
-    TRY(gemm(c, g));
+  std::vector<float> rec;
+  TRY(record_begin(c, i, std::min(mrow, ncol), rec));
+  int k = 0, nnz = 0, l = 0;
+  double f = 0;
+  bool sketched = false;
+  TRY(sketch_size(c, i, mrow, ncol, l));
+  if (l > 0) TRY(rsvd_try(c, i, false, mrow, ncol, l, sketched, k, f));
+  if (sketched) {
+    c->warm_dim[i] = 0;
   } else {
-    Span sp(c, TC_OTHER);
-    CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
-    c->stats.kernel_launches++;
-  }
-  int k, nnz = 0;
-  double f;
-  TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
-  TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
-  TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
-  {
+    TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+    if (c->warm_dim[i] == ncol && c->warm_side[i] == 'R') {
+      GemmArgs g;   // jw (column-major) = theta V_prev: row-major [ncol][mrow] = V^T theta^T
+      g.M = ncol; g.N = mrow; g.K = ncol;
+      g.A = c->warm[i].p; g.lda = ncol; g.opA = OP_N;
+      g.B = c->theta.p; g.ldb = ncol; g.opB = OP_T;
+      g.C = c->jw.p; g.ldc = mrow;
+      TRY(gemm(c, g));
+    } else {
+      Span sp(c, TC_OTHER);
+      CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
+    TRY(record_end(c, i, k, true, rec));
+    TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
+    TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
     Span sp(c, TC_SVD);
     CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
     c->stats.kernel_launches++;
   }
+  if (sketched) TRY(record_end(c, i, k, false, rec));
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
   GemmArgs g;   // A_{i+1} = A_i^+ theta / |S_k|
   g.M = k; g.N = ncol; g.K = mrow;
@@ -393,26 +638,35 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   if (c->xyk[i] != 'X') return fail(c, DMRGC_ESTATE, "left cache missing");
   int mrow, ncol;
   TRY(form_theta(c, i, mrow, ncol));
-  TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-  if (c->warm_dim[i] == mrow && c->warm_side[i] == 'L') {
-    GemmArgs g;   // jw (column-major) = theta^+ U_prev: row-major [mrow][ncol] = U^T conj(theta)
-    g.M = mrow; g.N = ncol; g.K = mrow;
-    g.A = c->warm[i].p; g.lda = mrow; g.opA = OP_N;
-    g.B = c->theta.p; g.ldb = ncol; g.opB = OP_R;
-    g.C = c->jw.p; g.ldc = ncol;
-    TRY(gemm(c, g));
+  std::vector<float> rec;
+  TRY(record_begin(c, i, std::min(mrow, ncol), rec));
+  int k = 0, nnz = 0, l = 0;
+  double f = 0;
+  bool sketched = false;
+  TRY(sketch_size(c, i, mrow, ncol, l));
+  if (l > 0) TRY(rsvd_try(c, i, true, mrow, ncol, l, sketched, k, f));
+  if (sketched) {
+    c->warm_dim[i] = 0;
+    TRY(record_end(c, i, k, false, rec));
   } else {
-    Span sp(c, TC_OTHER);
-    CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
-    c->stats.kernel_launches++;
-  }
-  int k, nnz = 0;
-  double f;
-  // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
-  TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
-  TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
-  TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
-  {
+    TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+    if (c->warm_dim[i] == mrow && c->warm_side[i] == 'L') {
+      GemmArgs g;   // jw (column-major) = theta^+ U_prev: row-major [mrow][ncol] = U^T conj(theta)
+      g.M = mrow; g.N = ncol; g.K = mrow;
+      g.A = c->warm[i].p; g.lda = mrow; g.opA = OP_N;
+      g.B = c->theta.p; g.ldb = ncol; g.opB = OP_R;
+      g.C = c->jw.p; g.ldc = ncol;
+      TRY(gemm(c, g));
+    } else {
+      Span sp(c, TC_OTHER);
+      CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
+    TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
+    TRY(record_end(c, i, k, true, rec));
+    TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
+    TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
     Span sp(c, TC_SVD);
     CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
     c->stats.kernel_launches++;
@@ -687,6 +941,10 @@ dmrgc_status dmrgc_default_options(dmrgc_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = DMRGC_FP64;
   opt->svd_mode = 0;
+  opt->rsvd_oversample = 8;
+  opt->rsvd_power_iters = 1;
+  opt->rsvd_tolerance = 0.0;
+  opt->log_rank_records = 0;
   opt->max_jacobi_sweeps = 40;
   return DMRGC_OK;
 }
@@ -706,7 +964,8 @@ bool valid_shape(int n_qubits, const dmrgc_grid* grid, int chi) {
 // largest one.
 dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int chi, const dmrgc_options& opt) {
   c->opt = opt;
-  if (c->opt.precision < 0 || c->opt.precision > 3 || c->opt.svd_mode != 0)
+  if (c->opt.precision < 0 || c->opt.precision > 3 || c->opt.svd_mode < 0 || c->opt.svd_mode > 2 ||
+      c->opt.rsvd_power_iters > 8)
     return fail(c, DMRGC_EINVAL, "bad options");
   c->N = n_qubits; c->chi = chi; c->rows = grid->rows; c->cols = grid->cols; c->m = n_qubits / 2;
   c->st = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
@@ -736,6 +995,15 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
   c->warm_dim.assign(n_qubits, 0); c->warm_side.assign(n_qubits, 0);
   c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);
   c->L = EnvRef(); c->R = EnvRef();
+  c->layer_no = 0;
+  c->visit_layer.assign(n_qubits, -1);
+  c->rs_fail.assign(n_qubits, -1);
+  c->kprev.assign(n_qubits, 0);
+  c->rs_ctr = 0;
+  c->rs_p = c->opt.rsvd_oversample > 0 ? c->opt.rsvd_oversample : 8;
+  c->rs_pow = c->opt.rsvd_power_iters >= 0 ? c->opt.rsvd_power_iters : 1;
+  c->rs_tol = c->opt.rsvd_tolerance > 0 ? c->opt.rsvd_tolerance : (c->fp64 ? 1e-6 : 2e-5);
+  c->rec_x.clear(); c->rec_y.clear();
   c->phase = 0; c->bond = 0; c->dir = -1; c->centre = 0;
   c->log_ft = 0.0; c->f_cur = 1.0;
   c->hist.clear();
@@ -771,6 +1039,33 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
   return DMRGC_OK;
 }
 
+dmrgc_status dmrgc_set_rank_model(dmrgc_ctx* c, const float* params) {
+  if (!c || !params) return DMRGC_EINVAL;
+  DevBuf tmp;
+  TRY(ensure(c, tmp, DMRGC_MLP_PARAMS * sizeof(float)));
+  TRY(ensure(c, c->mlp_w, DMRGC_MLP_PARAMS * 2));
+  cudaError_t e = cudaMemcpyAsync(tmp.p, params, DMRGC_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = mlp_to_bf16((const float*)tmp.p, c->mlp_w.p, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cudaFree(tmp.p);
+  tmp.p = nullptr;
+  if (e != cudaSuccess) return fail(c, DMRGC_ECUDA, cudaGetErrorString(e));
+  c->stats.kernel_launches++;
+  c->mlp_ready = true;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_rank_records(dmrgc_ctx* c, float* features, float* labels, int max, int* count) {
+  if (!c || !count || max < 0 || (max > 0 && (!features || !labels))) return DMRGC_EINVAL;
+  const int n = std::min<int>(max, (int)c->rec_y.size());
+  std::copy(c->rec_x.begin(), c->rec_x.begin() + (size_t)n * DMRGC_MLP_IN, features);
+  std::copy(c->rec_y.begin(), c->rec_y.begin() + n, labels);
+  c->rec_x.erase(c->rec_x.begin(), c->rec_x.begin() + (size_t)n * DMRGC_MLP_IN);
+  c->rec_y.erase(c->rec_y.begin(), c->rec_y.begin() + n);
+  *count = n;
+  return DMRGC_OK;
+}
+
 dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, const dmrgc_options* opt,
                              double* wall_seconds) {
   if (wall_seconds) *wall_seconds = 0.0;
@@ -793,7 +1088,8 @@ dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, 
   }
   dmrgc_options base;
   if (opt) base = *opt; else dmrgc_default_options(&base);
-  if (base.precision < 0 || base.precision > 3 || base.svd_mode != 0) return DMRGC_EINVAL;
+  // the learned mode needs a rank model per context: not offered here
+  if (base.precision < 0 || base.precision > 3 || base.svd_mode < 0 || base.svd_mode > 1) return DMRGC_EINVAL;
   if (count == 0) return DMRGC_OK;
   if (n_workers > count) n_workers = count;
   std::atomic<int> next{0};
@@ -855,6 +1151,7 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
     c->chiB = c->chiA;
   }
   c->hist.clear();
+  c->layer_no++;
   std::fill(c->warm_dim.begin(), c->warm_dim.end(), 0);
   TRY(build_mpo(c, gates, n_gates));
   std::fill(c->xyk.begin(), c->xyk.end(), 0);

@@ -101,6 +101,23 @@ cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, do
 cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void* res,
                            bool squared, int mode, void* out, bool fp64, cudaStream_t st);
 
+// Spectrum read-outs of a truncation result (k = kept count):
+// out32[j] = log10(s_mu^2 / sum_{nu<k} s_nu^2) at mu = round(j (k-1) / 31), j < 32;
+// *out = smallest r with sum_{mu<r} s_mu^2 >= frac * sum_{mu<k} s_mu^2.
+cudaError_t spectrum_summary(const void* res, int k, float* out32, cudaStream_t st);
+cudaError_t rank_label(const void* res, int k, double frac, int* out, cudaStream_t st);
+
+// n complex entries of unit variance, E|z|^2 = 1: Box-Muller on SplitMix64
+// uniforms at counters ctr0 + 2j, ctr0 + 2j + 1 (entry j).
+cudaError_t fill_gaussian(void* dst, long long n, bool fp64, unsigned long long seed,
+                          unsigned long long ctr0, cudaStream_t st);
+
+// Rank model (mlp.cu): BF16 copy of the FP32 parameters, and one inference
+// from 32 device floats (the spectrum summary) + 4 host extras.
+cudaError_t mlp_to_bf16(const float* params_dev, void* out_bf16, cudaStream_t st);
+cudaError_t mlp_infer_one(const void* w_bf16, const float* feat32, const float* extras, float* y,
+                          cudaStream_t st);
+
 // ---------------------------------------------------------------- MPO build
 
 struct GateDev {   // device copy of one gate, already in site order

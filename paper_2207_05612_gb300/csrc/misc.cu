@@ -2,6 +2,7 @@
 // physical-index-first permutation of MPS tensors, identities, norms, scaling.
 #include "common.cuh"
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -129,6 +130,43 @@ cudaError_t allow_dyn_smem(const void* fn) {
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
   done.emplace_back(dev, fn);
   return cudaSuccess;
+}
+
+namespace {
+
+__device__ __forceinline__ double mix_uniform(unsigned long long seed, unsigned long long ctr) {
+  // SplitMix64 (Steele, Lea, Flood 2014) at counter ctr, top 53 bits -> [0, 1)
+  unsigned long long z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename C2>
+__global__ void gaussian_kernel(C2* __restrict__ out, long long n, unsigned long long seed,
+                                unsigned long long ctr0) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    const double u1 = mix_uniform(seed, ctr0 + 2ull * j);
+    const double u2 = mix_uniform(seed, ctr0 + 2ull * j + 1ull);
+    const double rad = sqrt(-log1p(-u1));   // |z|^2 ~ Exp(1): E|z|^2 = 1
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[j].x = rad * cs;
+    out[j].y = rad * sn;
+  }
+}
+
+}  // namespace
+
+cudaError_t fill_gaussian(void* dst, long long n, bool fp64, unsigned long long seed,
+                          unsigned long long ctr0, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (fp64) gaussian_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<double2*>(dst), n, seed, ctr0);
+  else gaussian_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<float2*>(dst), n, seed, ctr0);
+  return cudaGetLastError();
 }
 
 cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* dst, cudaStream_t st) {

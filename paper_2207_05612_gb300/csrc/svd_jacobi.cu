@@ -948,12 +948,55 @@ cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, do
   int np = 1;
   while (np < n) np <<= 1;
   const size_t sm = (size_t)np * (sizeof(double) + sizeof(int));
-  if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(sort_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
+  if (sm > 48 * 1024 && (e = allow_dyn_smem((const void*)sort_trunc_kernel)) != cudaSuccess) return e;
   sort_trunc_kernel<<<1, 1024, sm, st>>>(r, s, perm, s, n, chi, rel_cut, squared ? 1 : 0, tie_rel,
                                          fro2, zero_rel);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// 32 samples of log10(s_mu^2 / sum_{nu<k} s_nu^2) at mu_j = round(j (k-1) / 31)
+__global__ void spectrum_summary_kernel(const TruncResult* __restrict__ r, int k, float* __restrict__ out) {
+  const double* s = reinterpret_cast<const double*>(r + 1);
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < k; ++i) t += s[i] * s[i];
+    tot = t;
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < 32) {
+    const int mu = k > 1 ? (int)lrint((double)j * (k - 1) / 31.0) : 0;
+    const double q = tot > 0 ? s[mu] * s[mu] / tot : 0.0;
+    out[j] = (float)(q > 1e-30 ? log10(q) : -30.0);
+  }
+}
+
+// smallest r with sum_{mu<r} s_mu^2 >= frac * sum_{mu<k} s_mu^2
+__global__ void rank_label_kernel(const TruncResult* __restrict__ r, int k, double frac, int* __restrict__ out) {
+  const double* s = reinterpret_cast<const double*>(r + 1);
+  double tot = 0;
+  for (int i = 0; i < k; ++i) tot += s[i] * s[i];
+  double run = 0;
+  int rr = k;
+  for (int i = 0; i < k; ++i) {
+    run += s[i] * s[i];
+    if (run >= frac * tot) { rr = i + 1; break; }
+  }
+  *out = rr;
+}
+
+}  // namespace
+
+cudaError_t spectrum_summary(const void* res, int k, float* out32, cudaStream_t st) {
+  spectrum_summary_kernel<<<1, 32, 0, st>>>(reinterpret_cast<const TruncResult*>(res), k, out32);
+  return cudaGetLastError();
+}
+
+cudaError_t rank_label(const void* res, int k, double frac, int* out, cudaStream_t st) {
+  rank_label_kernel<<<1, 1, 0, st>>>(reinterpret_cast<const TruncResult*>(res), k, frac, out);
   return cudaGetLastError();
 }
 
