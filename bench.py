@@ -375,7 +375,10 @@ def main(argv=None):
                          "other": st["other_ms"],
                          "gemm_tflops": st["gemm_flops"] / max(gemm_s, 1e-12) / 1e12,
                          "svd_tflops": st["svd_flops"] / max(svd_s, 1e-12) / 1e12,
-                         "jacobi_sweeps_per_svd": st["jacobi_sweeps"] / max(1, st["svd_launches"] / 4)},
+                         "jacobi_sweeps_per_svd": st["jacobi_sweeps"] / max(1, st["svd_launches"] / 4),
+                         "jacobi_sweeps_per_update": st["jacobi_sweeps"] / max(1, st["updates"]),
+                         "warm_starts": int(st["warm_starts"]),
+                         "warm_sweeps_per_svd": st["warm_sweeps"] / max(1, st["warm_starts"])},
         "state": {"max_chi": r["max_chi"], "max_D": r["max_D"]},
     }
     print(json.dumps(line))

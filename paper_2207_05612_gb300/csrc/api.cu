@@ -190,8 +190,10 @@ dmrgc_status sync(dmrgc_ctx* c) {
 
 // ---- GEMM dispatch
 
-cudaError_t run_gemm(int precision, const GemmArgs& g, TcWork* w, int* err_dev, cudaStream_t st) {
-  if (precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3) return gemm_tc(g, precision, *w, err_dev, st);
+cudaError_t run_gemm(int precision, const GemmArgs& g, TcWork* w, int* err_dev, cudaStream_t st,
+                     int* launches = nullptr) {
+  if (precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3) return gemm_tc(g, precision, *w, err_dev, st, launches);
+  if (launches) *launches = 1;
   return gemm_simt(g, precision == DMRGC_FP64, st);
 }
 
@@ -203,9 +205,10 @@ dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
   }
   const double fl = 8.0 * g.M * (double)g.N * g.K * g.b1 * g.b2;
   Span sp(c, TC_GEMM, fl);
-  CK(run_gemm(c->opt.precision, g, &c->tcw, (int*)c->tcerr.p, c->st));
+  int launches = 0;
+  CK(run_gemm(c->opt.precision, g, &c->tcw, (int*)c->tcerr.p, c->st, &launches));
   c->stats.gemm_launches++;
-  c->stats.kernel_launches++;
+  c->stats.kernel_launches += launches;
   return DMRGC_OK;
 }
 
@@ -316,14 +319,68 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
 // orthogonal set of columns, so few sweeps remain.  Only complete bases (as
 // many vectors as the space's dimension) are stored; the rotation is unitary,
 // so the SVD it leads to is the same.
+dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r, int mode = 0);
+
+// Complete the nnz orthonormal columns of V (column-major dim x dim) to a
+// unitary: Gaussian columns, projected twice on the complement of the first
+// nnz (classical Gram-Schmidt with re-orthogonalisation, as GEMMs), then
+// orthonormalised among themselves.  ok = false if they lose rank.
+dmrgc_status complete_basis(dmrgc_ctx* c, void* V, int dim, int nnz, bool& ok) {
+  ok = false;
+  const int r = dim - nnz;
+  const size_t es = c->esz;
+  char* rt = static_cast<char*>(V) + (size_t)nnz * dim * es;   // row-major [r][dim]
+  TRY(ensure(c, c->rs_b, (size_t)r * nnz * es));
+  TRY(ensure(c, c->rs_y, (size_t)r * dim * es));
+  TRY(ensure(c, c->rs_q, (size_t)r * dim * es));
+  {
+    Span sp(c, TC_SVD);
+    CK(fill_gaussian(rt, (long long)r * dim, c->fp64, c->opt.seed ^ 0x5bd1e995ull, c->rs_ctr, c->st));
+    c->stats.kernel_launches++;
+  }
+  c->rs_ctr += 2ull * r * dim;
+  for (int pass = 0; pass < 2; ++pass) {
+    GemmArgs g;   // P^T = R^T conj(Vg) [r][nnz]
+    g.M = r; g.N = nnz; g.K = dim;
+    g.A = rt; g.lda = dim; g.opA = OP_N;
+    g.B = V; g.ldb = dim; g.opB = OP_C;
+    g.C = c->rs_b.p; g.ldc = nnz;
+    TRY(gemm(c, g));
+    GemmArgs h;   // R^T -= P^T Vg^T
+    h.M = r; h.N = dim; h.K = nnz;
+    h.A = c->rs_b.p; h.lda = nnz; h.opA = OP_N;
+    h.B = V; h.ldb = dim; h.opB = OP_N;
+    h.C = rt; h.ldc = dim;
+    h.alpha_re = -1.0;
+    h.beta_one = true;
+    TRY(gemm(c, h));
+  }
+  CK(cudaMemcpyAsync(c->rs_y.p, rt, (size_t)r * dim * es, cudaMemcpyDeviceToDevice, c->st));
+  int rr = 0;
+  TRY(orth_columns(c, c->rs_y.p, dim, r, c->rs_q.p, rr, 1));
+  if (rr != r) return DMRGC_OK;
+  CK(cudaMemcpyAsync(rt, c->rs_q.p, (size_t)r * dim * es, cudaMemcpyDeviceToDevice, c->st));
+  ok = true;
+  return DMRGC_OK;
+}
+
+// Call after the update's own gather: completing a basis reuses the spectrum
+// buffer.  Bases missing more than a quarter of their vectors are not stored.
 dmrgc_status warm_store(dmrgc_ctx* c, int bond, char side, int dim, int ncols, int nnz) {
   c->warm_dim[bond] = 0;
-  if (c->fp64 || nnz != dim || dim < 16) return DMRGC_OK;   // FP64 runs keep the plain iteration
+  if (c->fp64 || dim < 16 || nnz < 1 || dim - nnz > dim / 4) return DMRGC_OK;   // FP64 keeps the plain iteration
   TRY(ensure(c, c->warm[bond], (size_t)dim * dim * c->esz));
-  Span sp(c, TC_SVD);
-  // the first `dim` sorted columns of jw, normalised, column-major [dim x dim]
-  CK(gather_columns(c->jw.p, dim, ncols, dim, c->tres.p, false, 1, c->warm[bond].p, c->fp64, c->st));
-  c->stats.kernel_launches++;
+  {
+    Span sp(c, TC_SVD);
+    // the nnz columns above the zero level, normalised, column-major [dim x nnz]
+    CK(gather_columns(c->jw.p, dim, ncols, nnz, c->tres.p, false, 1, c->warm[bond].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  if (nnz < dim) {
+    bool ok = false;
+    TRY(complete_basis(c, c->warm[bond].p, dim, nnz, ok));
+    if (!ok) return DMRGC_OK;
+  }
   c->warm_dim[bond] = dim;
   c->warm_side[bond] = side;
   return DMRGC_OK;
@@ -367,13 +424,14 @@ dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
 
 // orthonormal basis of the columns of W (column-major rows x cols): every
 // direction above the numerical-zero level, out row-major [rows][r]
-dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r) {
+// (mode 1: out column-major [rows][r])
+dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r, int mode) {
   int k = 0, nnz = 0;
   double f = 0;
   TRY(svd_columns(c, rows, cols, 0.0, false, 0.0, k, f, &nnz, nullptr, W, cols));
   r = k;
   Span sp(c, TC_SVD);
-  CK(gather_columns(W, rows, cols, k, c->tres.p, false, 0, out, c->fp64, c->st));
+  CK(gather_columns(W, rows, cols, k, c->tres.p, false, mode, out, c->fp64, c->st));
   c->stats.kernel_launches++;
   return DMRGC_OK;
 }
@@ -583,7 +641,8 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
     c->warm_dim[i] = 0;
   } else {
     TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    if (c->warm_dim[i] == ncol && c->warm_side[i] == 'R') {
+    const bool warm = c->warm_dim[i] == ncol && c->warm_side[i] == 'R';
+    if (warm) {
       GemmArgs g;   // jw (column-major) = theta V_prev: row-major [ncol][mrow] = V^T theta^T
       g.M = ncol; g.N = mrow; g.K = ncol;
       g.A = c->warm[i].p; g.lda = ncol; g.opA = OP_N;
@@ -595,13 +654,17 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
       CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
+    const long long sw0 = c->stats.jacobi_sweeps;
     TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
+    if (warm) { c->stats.warm_starts++; c->stats.warm_sweeps += c->stats.jacobi_sweeps - sw0; }
     TRY(record_end(c, i, k, true, rec));
-    TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
     TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
-    Span sp(c, TC_SVD);
-    CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
-    c->stats.kernel_launches++;
+    {
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
   }
   if (sketched) TRY(record_end(c, i, k, false, rec));
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
@@ -650,7 +713,8 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
     TRY(record_end(c, i, k, false, rec));
   } else {
     TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    if (c->warm_dim[i] == mrow && c->warm_side[i] == 'L') {
+    const bool warm = c->warm_dim[i] == mrow && c->warm_side[i] == 'L';
+    if (warm) {
       GemmArgs g;   // jw (column-major) = theta^+ U_prev: row-major [mrow][ncol] = U^T conj(theta)
       g.M = mrow; g.N = ncol; g.K = mrow;
       g.A = c->warm[i].p; g.lda = mrow; g.opA = OP_N;
@@ -663,13 +727,17 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
       c->stats.kernel_launches++;
     }
     // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
+    const long long sw0 = c->stats.jacobi_sweeps;
     TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
+    if (warm) { c->stats.warm_starts++; c->stats.warm_sweeps += c->stats.jacobi_sweeps - sw0; }
     TRY(record_end(c, i, k, true, rec));
-    TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
     TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
-    Span sp(c, TC_SVD);
-    CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
-    c->stats.kernel_launches++;
+    {
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
   }
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
   GemmArgs g;   // A_i = theta A_{i+1}^+ / |S_k|

@@ -57,7 +57,9 @@ struct TcWork {
   cudaError_t ensure(int i, size_t bytes);
   void release();
 };
-cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, cudaStream_t st);
+// *launches (optional): kernels launched (operand packs, C clear, the GEMM)
+cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, cudaStream_t st,
+                    int* launches = nullptr);
 
 // --------------------------------------------------------------------- SVD
 

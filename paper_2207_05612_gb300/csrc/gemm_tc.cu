@@ -436,7 +436,7 @@ int sm_count() {
 }
 
 template <int ESZ>
-cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st) {
+cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, int* launches) {
   const int esz = ESZ;
   const int align = 16 / esz;
   const int kp = ((2 * g.K + align - 1) / align) * align;
@@ -498,6 +498,7 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st) 
   a.split = split;
   a.per = (a.ktiles + split - 1) / split;
   a.mode = split > 1 ? 2 : (g.beta_one ? 1 : 0);
+  if (launches) *launches = 3 + (split > 1 && !g.beta_one ? 1 : 0);
   if (split > 1 && !g.beta_one) {
     dim3 zg(64, 1, (unsigned)(g.b1 * g.b2));
     zero_c_kernel<<<zg, 256, 0, st>>>((float2*)g.C, g.M, g.N, g.ldc, g.sC1, g.sC2, g.b2);
@@ -539,10 +540,11 @@ void TcWork::release() {
   }
 }
 
-cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, cudaStream_t st) {
+cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, cudaStream_t st, int* launches) {
+  if (launches) *launches = 0;
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.b1 <= 0 || g.b2 <= 0) return cudaSuccess;
-  if (precision == DMRGC_BF16X3) return run_tc<2>(g, w, err_dev, st);
-  if (precision == DMRGC_TF32X3) return run_tc<4>(g, w, err_dev, st);
+  if (precision == DMRGC_BF16X3) return run_tc<2>(g, w, err_dev, st, launches);
+  if (precision == DMRGC_TF32X3) return run_tc<4>(g, w, err_dev, st, launches);
   return cudaErrorInvalidValue;
 }
 

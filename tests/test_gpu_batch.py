@@ -29,7 +29,7 @@ def test_batch_matches_single_context_and_oracle():
     for (rows, cols, chi, cyc, seed), circ, r in zip(CASES, circs, res):
         n = rows * cols
         assert r.status == 0
-        assert r.updates == len(circ.layers) * 2 * 2 * (n - 1)
+        assert r.updates == len(circ.layers) * 2 * (n - 1)
         assert 0 <= r.worker < 3
         ctx, per = gpu_run(circ, chi, precision=0)
         assert abs(r.log_F_tilde - per[-1]["log_ft"]) < 1e-12
