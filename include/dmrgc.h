@@ -112,8 +112,6 @@ typedef struct {
   long long kernel_launches;    /* every kernel the library launched */
   long long rsvd_attempts;      /* randomized SVDs tried (svd_mode 1, 2) */
   long long rsvd_accepted;      /* of which accepted (the rest fell back to Jacobi) */
-  long long warm_starts;        /* Jacobi SVDs started from the bond's previous singular basis */
-  long long warm_sweeps;        /* Jacobi sweeps those took */
 } dmrgc_stats;
 
 /* Fill *opt with defaults (FP64, Jacobi, default cutoffs, default stream). */

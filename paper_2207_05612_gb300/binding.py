@@ -48,8 +48,7 @@ class Stats(C.Structure):
                 ("svd_ms", C.c_double), ("svd_flops", C.c_double), ("svd_launches", C.c_longlong),
                 ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
                 ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong),
-                ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong),
-                ("warm_starts", C.c_longlong), ("warm_sweeps", C.c_longlong)]
+                ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong)]
 
 
 class BatchItem(C.Structure):

@@ -50,9 +50,7 @@ struct dmrgc_ctx {
   double sweep_cut = 1e-12, zip_cut = 1e-5, zero_rel = 1e-13, tie_rel = 1e-10;
   int max_jsweeps = 40;
   std::vector<int> order, site_of;
-  std::vector<DevBuf> A, B, Wx, Wy, XY, E, warm;
-  std::vector<int> warm_dim;   // per bond: dimension of the stored singular basis (0 = none)
-  std::vector<char> warm_side; // 'L': (a s1) basis from a left-to-right SVD; 'R': (s2 c) basis
+  std::vector<DevBuf> A, B, Wx, Wy, XY, E;
   std::vector<int> chiA, chiB, D;     // N+1 entries each
   std::vector<char> xyk;
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
@@ -311,81 +309,6 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   return DMRGC_OK;
 }
 
-// Warm start of the Jacobi iteration at a bond.  Consecutive visits of a bond
-// come from opposite directions, and the basis on the side that has not changed
-// since the last visit is exactly the singular basis that SVD computed (left
-// vectors U after a left-to-right update, right vectors V after a
-// right-to-left one).  Rotating the Jacobi input by it leaves a nearly
-// orthogonal set of columns, so few sweeps remain.  Only complete bases (as
-// many vectors as the space's dimension) are stored; the rotation is unitary,
-// so the SVD it leads to is the same.
-dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r, int mode = 0);
-
-// Complete the nnz orthonormal columns of V (column-major dim x dim) to a
-// unitary: Gaussian columns, projected twice on the complement of the first
-// nnz (classical Gram-Schmidt with re-orthogonalisation, as GEMMs), then
-// orthonormalised among themselves.  ok = false if they lose rank.
-dmrgc_status complete_basis(dmrgc_ctx* c, void* V, int dim, int nnz, bool& ok) {
-  ok = false;
-  const int r = dim - nnz;
-  const size_t es = c->esz;
-  char* rt = static_cast<char*>(V) + (size_t)nnz * dim * es;   // row-major [r][dim]
-  TRY(ensure(c, c->rs_b, (size_t)r * nnz * es));
-  TRY(ensure(c, c->rs_y, (size_t)r * dim * es));
-  TRY(ensure(c, c->rs_q, (size_t)r * dim * es));
-  {
-    Span sp(c, TC_SVD);
-    CK(fill_gaussian(rt, (long long)r * dim, c->fp64, c->opt.seed ^ 0x5bd1e995ull, c->rs_ctr, c->st));
-    c->stats.kernel_launches++;
-  }
-  c->rs_ctr += 2ull * r * dim;
-  for (int pass = 0; pass < 2; ++pass) {
-    GemmArgs g;   // P^T = R^T conj(Vg) [r][nnz]
-    g.M = r; g.N = nnz; g.K = dim;
-    g.A = rt; g.lda = dim; g.opA = OP_N;
-    g.B = V; g.ldb = dim; g.opB = OP_C;
-    g.C = c->rs_b.p; g.ldc = nnz;
-    TRY(gemm(c, g));
-    GemmArgs h;   // R^T -= P^T Vg^T
-    h.M = r; h.N = dim; h.K = nnz;
-    h.A = c->rs_b.p; h.lda = nnz; h.opA = OP_N;
-    h.B = V; h.ldb = dim; h.opB = OP_N;
-    h.C = rt; h.ldc = dim;
-    h.alpha_re = -1.0;
-    h.beta_one = true;
-    TRY(gemm(c, h));
-  }
-  CK(cudaMemcpyAsync(c->rs_y.p, rt, (size_t)r * dim * es, cudaMemcpyDeviceToDevice, c->st));
-  int rr = 0;
-  TRY(orth_columns(c, c->rs_y.p, dim, r, c->rs_q.p, rr, 1));
-  if (rr != r) return DMRGC_OK;
-  CK(cudaMemcpyAsync(rt, c->rs_q.p, (size_t)r * dim * es, cudaMemcpyDeviceToDevice, c->st));
-  ok = true;
-  return DMRGC_OK;
-}
-
-// Call after the update's own gather: completing a basis reuses the spectrum
-// buffer.  Bases missing more than a quarter of their vectors are not stored.
-dmrgc_status warm_store(dmrgc_ctx* c, int bond, char side, int dim, int ncols, int nnz) {
-  c->warm_dim[bond] = 0;
-  if (c->fp64 || dim < 16 || nnz < 1 || dim - nnz > dim / 4) return DMRGC_OK;   // FP64 keeps the plain iteration
-  TRY(ensure(c, c->warm[bond], (size_t)dim * dim * c->esz));
-  {
-    Span sp(c, TC_SVD);
-    // the nnz columns above the zero level, normalised, column-major [dim x nnz]
-    CK(gather_columns(c->jw.p, dim, ncols, nnz, c->tres.p, false, 1, c->warm[bond].p, c->fp64, c->st));
-    c->stats.kernel_launches++;
-  }
-  if (nnz < dim) {
-    bool ok = false;
-    TRY(complete_basis(c, c->warm[bond].p, dim, nnz, ok));
-    if (!ok) return DMRGC_OK;
-  }
-  c->warm_dim[bond] = dim;
-  c->warm_side[bond] = side;
-  return DMRGC_OK;
-}
-
 // theta[(a s1)][(s2 c)] = X_i Y_{i+1}^T
 dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
   const int a = c->chiA[i], cc = c->chiA[i + 2];
@@ -425,7 +348,7 @@ dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
 // orthonormal basis of the columns of W (column-major rows x cols): every
 // direction above the numerical-zero level, out row-major [rows][r]
 // (mode 1: out column-major [rows][r])
-dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r, int mode) {
+dmrgc_status orth_columns(dmrgc_ctx* c, void* W, int rows, int cols, void* out, int& r, int mode = 0) {
   int k = 0, nnz = 0;
   double f = 0;
   TRY(svd_columns(c, rows, cols, 0.0, false, 0.0, k, f, &nnz, nullptr, W, cols));
@@ -638,35 +561,21 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   TRY(sketch_size(c, i, mrow, ncol, l));
   if (l > 0) TRY(rsvd_try(c, i, false, mrow, ncol, l, sketched, k, f));
   if (sketched) {
-    c->warm_dim[i] = 0;
+    TRY(record_end(c, i, k, false, rec));
   } else {
     TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    const bool warm = c->warm_dim[i] == ncol && c->warm_side[i] == 'R';
-    if (warm) {
-      GemmArgs g;   // jw (column-major) = theta V_prev: row-major [ncol][mrow] = V^T theta^T
-      g.M = ncol; g.N = mrow; g.K = ncol;
-      g.A = c->warm[i].p; g.lda = ncol; g.opA = OP_N;
-      g.B = c->theta.p; g.ldb = ncol; g.opB = OP_T;
-      g.C = c->jw.p; g.ldc = mrow;
-      TRY(gemm(c, g));
-    } else {
+    {
       Span sp(c, TC_OTHER);
       CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
-    const long long sw0 = c->stats.jacobi_sweeps;
     TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
-    if (warm) { c->stats.warm_starts++; c->stats.warm_sweeps += c->stats.jacobi_sweeps - sw0; }
     TRY(record_end(c, i, k, true, rec));
     TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
-    {
-      Span sp(c, TC_SVD);
-      CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
-      c->stats.kernel_launches++;
-    }
-    TRY(warm_store(c, i, 'L', mrow, ncol, nnz));
+    Span sp(c, TC_SVD);
+    CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
   }
-  if (sketched) TRY(record_end(c, i, k, false, rec));
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
   GemmArgs g;   // A_{i+1} = A_i^+ theta / |S_k|
   g.M = k; g.N = ncol; g.K = mrow;
@@ -709,35 +618,21 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   TRY(sketch_size(c, i, mrow, ncol, l));
   if (l > 0) TRY(rsvd_try(c, i, true, mrow, ncol, l, sketched, k, f));
   if (sketched) {
-    c->warm_dim[i] = 0;
     TRY(record_end(c, i, k, false, rec));
   } else {
     TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    const bool warm = c->warm_dim[i] == mrow && c->warm_side[i] == 'L';
-    if (warm) {
-      GemmArgs g;   // jw (column-major) = theta^+ U_prev: row-major [mrow][ncol] = U^T conj(theta)
-      g.M = mrow; g.N = ncol; g.K = mrow;
-      g.A = c->warm[i].p; g.lda = mrow; g.opA = OP_N;
-      g.B = c->theta.p; g.ldb = ncol; g.opB = OP_R;
-      g.C = c->jw.p; g.ldc = ncol;
-      TRY(gemm(c, g));
-    } else {
+    {
       Span sp(c, TC_OTHER);
       CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
     // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
-    const long long sw0 = c->stats.jacobi_sweeps;
     TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
-    if (warm) { c->stats.warm_starts++; c->stats.warm_sweeps += c->stats.jacobi_sweeps - sw0; }
     TRY(record_end(c, i, k, true, rec));
     TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
-    {
-      Span sp(c, TC_SVD);
-      CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
-      c->stats.kernel_launches++;
-    }
-    TRY(warm_store(c, i, 'R', ncol, mrow, nnz));
+    Span sp(c, TC_SVD);
+    CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
   }
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
   GemmArgs g;   // A_i = theta A_{i+1}^+ / |S_k|
@@ -992,7 +887,7 @@ dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
 
 dmrgc_ctx::~dmrgc_ctx() {
   auto fr = [](DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; };
-  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &warm})
+  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
                     &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr})
@@ -1057,10 +952,9 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
     }
   c->site_of.assign(n_qubits, 0);
   for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
-  for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E, &c->warm})
+  for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E})
     if ((int)v->size() < n_qubits) v->resize(n_qubits);
   c->xyk.assign(n_qubits, 0);
-  c->warm_dim.assign(n_qubits, 0); c->warm_side.assign(n_qubits, 0);
   c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);
   c->L = EnvRef(); c->R = EnvRef();
   c->layer_no = 0;
@@ -1220,7 +1114,6 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
   }
   c->hist.clear();
   c->layer_no++;
-  std::fill(c->warm_dim.begin(), c->warm_dim.end(), 0);
   TRY(build_mpo(c, gates, n_gates));
   std::fill(c->xyk.begin(), c->xyk.end(), 0);
   TRY(zip_guess(c));

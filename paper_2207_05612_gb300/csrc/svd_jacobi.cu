@@ -594,27 +594,17 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
   // (u, v) = (first, second) column: the same arithmetic in both warps of the
   // pair.  Packed FP32x2 FMAs: nu = (sum ux^2, sum uy^2), nv likewise,
   // p1 = (sum ux vx, sum uy vy), p2 = (sum ux vy, sum uy vx).
-  static_assert(E % 2 == 0, "E must be even");
-  // two accumulator sets (even / odd e) halve the dependent FMA chains
   float2 nu{0.f, 0.f}, nv{0.f, 0.f}, p1{0.f, 0.f}, p2{0.f, 0.f};
-  float2 nu2{0.f, 0.f}, nv2{0.f, 0.f}, q1{0.f, 0.f}, q2{0.f, 0.f};
 #pragma unroll
-  for (int e = 0; e < E; e += 2) {
+  for (int e = 0; e < E; ++e) {
     const float2 u = FIRST ? x[e] : y[e];
     const float2 v = FIRST ? y[e] : x[e];
     nu = __ffma2_rn(u, u, nu);
     nv = __ffma2_rn(v, v, nv);
     p1 = __ffma2_rn(u, v, p1);
     p2 = __ffma2_rn(u, make_float2(v.y, v.x), p2);
-    const float2 u2 = FIRST ? x[e + 1] : y[e + 1];
-    const float2 v2 = FIRST ? y[e + 1] : x[e + 1];
-    nu2 = __ffma2_rn(u2, u2, nu2);
-    nv2 = __ffma2_rn(v2, v2, nv2);
-    q1 = __ffma2_rn(u2, v2, q1);
-    q2 = __ffma2_rn(u2, make_float2(v2.y, v2.x), q2);
   }
-  float al = (nu.x + nu.y) + (nu2.x + nu2.y), be = (nv.x + nv.y) + (nv2.x + nv2.y);
-  float gr = (p1.x + p1.y) + (q1.x + q1.y), gi = (p2.x - p2.y) + (q2.x - q2.y);
+  float al = nu.x + nu.y, be = nv.x + nv.y, gr = p1.x + p1.y, gi = p2.x - p2.y;
   al = warp_sum(al);
   be = warp_sum(be);
   gr = warp_sum(gr);

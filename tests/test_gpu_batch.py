@@ -52,14 +52,20 @@ def test_batch_is_independent_of_worker_count():
         assert a.updates == b.updates
 
 
-def test_batch_mixed_precision_and_reuse_across_sizes():
-    """A worker reuses its context for instances that grow and shrink; the
-    complex64 tensor-core path gives the single-context result."""
+def test_batch_reuse_across_sizes_and_mixed_precision():
+    """One worker reuses its context for instances that grow and shrink: FP64
+    results equal single-context runs; in BF16x3 the exact-regime instances
+    keep F_tilde = 1 (truncated ones are compared nowhere bit for bit: the
+    tensor-core split-K order is not fixed)."""
     cases = [(4, 6, 64, 8, 11), (2, 3, 4, 4, 12), (4, 6, 32, 8, 13), (3, 4, 64, 6, 14)]
-    circs, res, _ = _batch(cases, workers=1, precision=1)
+    circs, res, _ = _batch(cases, workers=1, precision=0)
     for (rows, cols, chi, cyc, seed), circ, r in zip(cases, circs, res):
         assert r.status == 0
-        ctx, per = gpu_run(circ, chi, precision=1)
+        ctx, per = gpu_run(circ, chi, precision=0)
         ctx.close()
-        assert abs(r.log_F_tilde - per[-1]["log_ft"]) < 3e-4 * max(1.0, abs(per[-1]["log_ft"]))
-
+        assert abs(r.log_F_tilde - per[-1]["log_ft"]) < 1e-12
+    exact = [(3, 4, 64, 8, 15), (2, 3, 8, 6, 16), (4, 4, 256, 6, 17), (2, 4, 16, 6, 18)]
+    circs, res, _ = _batch(exact, workers=2, precision=1)
+    for r in res:
+        assert r.status == 0
+        assert abs(r.log_F_tilde) < 1e-4

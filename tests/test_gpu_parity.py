@@ -262,22 +262,3 @@ def test_qaoa_sampled_cut_value(prec, chi):
     cut = np.sum(smp[:, e[:, 0]] != smp[:, e[:, 1]], axis=1)
     assert abs(cut.mean() - exp_c) < 4 * cut.std() / np.sqrt(len(cut)) + 1e-9
 
-
-@pytest.mark.parametrize("prec", [1, 2])
-def test_warm_started_jacobi_keeps_the_result(prec):
-    """Saturated complex64 run on 4x6: Jacobi SVDs started from the bond's
-    previous singular basis (completed to a unitary where its last vectors
-    fell below the zero level) happen, take fewer sweeps than cold ones, and
-    leave F_tilde within the mixed-precision bound of the FP64 run."""
-    circ = sc.random_circuit(4, 6, 12, seed=4)
-    ref, _ = gpu_run(circ, 32, precision=0)
-    ctx, _ = gpu_run(circ, 32, precision=prec, timing=True)
-    st = ctx.stats()
-    assert st["warm_starts"] > 0
-    cold = (st["jacobi_sweeps"] - st["warm_sweeps"]) / max(1, st["updates"] - st["warm_starts"])
-    warm = st["warm_sweeps"] / st["warm_starts"]
-    print(f"warm starts {st['warm_starts']}/{st['updates']}: {warm:.2f} vs {cold:.2f} sweeps")
-    assert warm < cold
-    lf, _ = ctx.fidelity()
-    lr, _ = ref.fidelity()
-    assert abs(lf - lr) <= 1e-2 * abs(lr)
