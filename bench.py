@@ -265,6 +265,8 @@ def main(argv=None):
     ap.add_argument("--chi", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
+                    help="complex64 Jacobi kernel for m <= 1024")
     ap.add_argument("--records", type=int, default=20000, help="learned: training records to log")
     ap.add_argument("--eval-layers", type=int, default=4, help="learned: layers of the random circuit to run")
     ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned"],
@@ -279,6 +281,9 @@ def main(argv=None):
     ap.add_argument("--fidelity-report", action="store_true",
                     help="report F_tilde of every precision on the 24-qubit version and the oracle")
     args = ap.parse_args(argv)
+    if args.impl == "ours":
+        from paper_2207_05612_gb300 import binding
+        binding.dmrgc_set_jacobi_kernel(0 if args.jacobi == "wp4" else 1)
     if args.fidelity_report:
         return fidelity_report(args)
     if args.workload == "qaoa":
@@ -292,6 +297,7 @@ def main(argv=None):
     config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
               "cycles_per_step": 2, "sweeps_per_step": 2,
               "updates_per_step": 2 * (args.rows * args.cols - 1),
+              "jacobi_kernel": args.jacobi,
               "l2": "inputs larger than L2 (environment caches of GBs), no flush"}
 
     if args.impl == "reference":

@@ -198,6 +198,13 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out);
 
+/* Tuning: the Jacobi kernel for complex64 matrices of at most 1024 rows
+ * (process-wide).  0 (default): column pairs, one warp per column, two
+ * 4-column blocks per CTA; 1: 8 x 8 Gram blocks, rows spread over 512 threads,
+ * one Jacobi sweep of the Gram per round.  Both compute the same
+ * decomposition to working precision.  Other values: DMRGC_EINVAL. */
+dmrgc_status dmrgc_set_jacobi_kernel(int variant);
+
 /* ---- Rank model (svd_mode 2)
  *
  * Not in the paper: a multilayer perceptron that predicts, for the next update

@@ -97,13 +97,14 @@ def lib():
         L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), P(C.c_double)]
+        L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
         fp = C.c_void_p
         L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
         L.dmrgc_rank_records.argtypes = [C.c_void_p, fp, fp, C.c_int, P(C.c_int)]
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+        for name in ("dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
                      "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
@@ -344,6 +345,11 @@ def dmrgc_mlp_predict(params: np.ndarray, x: np.ndarray, bf16: bool = True) -> n
     _check(lib().dmrgc_mlp_predict(p.ctypes.data, x.ctypes.data, x.shape[0], 1 if bf16 else 0,
                                    out.ctypes.data))
     return out
+
+
+def dmrgc_set_jacobi_kernel(variant: int) -> None:
+    """0: column-pair Jacobi kernel (default); 1: Gram-block kernel."""
+    _check(lib().dmrgc_set_jacobi_kernel(int(variant)))
 
 
 class Context:

@@ -17,6 +17,7 @@
 // update and theta^+ for a right-to-left one.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -736,6 +737,262 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
   }
 }
 
+// ---- block Jacobi on 8 x 8 Gram matrices (complex64, m <= 512 RPT)
+//
+// One CTA per pair of 4-column blocks (8 columns), 512 threads; thread t holds
+// rows t + 512 k (k < RPT) of the 8 columns in registers, so rows are spread
+// over 16 warps and no column crosses a warp boundary in the arithmetic.  Per
+// round:
+//  1. the 8 x 8 Gram matrix X^+ X of the block pair (8 real diagonal and 28
+//     complex entries, 64 floats per thread), reduced in the warp by a
+//     reduce-scatter butterfly (64 -> 2 values per lane) and over the warps
+//     through shared memory;
+//  2. warp 0 runs one cyclic Jacobi sweep on the Gram (7 steps of 4 disjoint
+//     pairs, the round-robin order on 8 indices).  Each pair uses the column
+//     kernels' rotation (same zero level, threshold and formulas); the
+//     rotation is applied to the Gram on both sides and accumulated in V;
+//  3. every thread replaces its rows by X V.
+// Pairs inside a block are revisited every round; pairs across blocks meet
+// once per sweep of the block round-robin.  The sweep ends, like the column
+// kernels, when its largest rotated |gamma| / sqrt(alpha beta) is below the
+// threshold.
+
+// the e-th pair (i < j) of 8 indices in row order: (0,1), (0,2), ..., (6,7)
+__device__ __forceinline__ void pair_index(int e, int& i, int& j) {
+  i = 0;
+  int rowlen = 7;
+  while (e >= rowlen) { e -= rowlen; ++i; --rowlen; }
+  j = i + 1 + e;
+}
+
+// role of index x in step s of the 8-index round-robin: partner, first (p) or second (q)
+__device__ __forceinline__ void step_role(int s, int x, int& partner, int& pair, bool& first) {
+  partner = x; pair = 0; first = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int a, b;
+    round_robin_pair(s, k, 8, a, b);
+    if (a == x) { partner = b; pair = k; first = true; }
+    if (b == x) { partner = a; pair = k; first = false; }
+  }
+}
+
+// R_{x x} (self) and R_{partner, x} (other) of the 2x2 rotation with
+// parameters (c, s, e^{-i phi} = er + i ei):  first: c, -s e^{-i phi};
+// second: c e^{-i phi}, s.
+__device__ __forceinline__ void rot_coeffs(const float4 r, bool first, float2& self, float2& other) {
+  if (first) { self = make_float2(r.x, 0.f); other = make_float2(-r.y * r.z, -r.y * r.w); }
+  else { self = make_float2(r.x * r.z, r.x * r.w); other = make_float2(r.y, 0.f); }
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cmulcf(float2 a, float2 b) {   // conj(a) b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(512, 1) jacobi_gram_kernel(float2* __restrict__ G, int m, int n, int nblk,
+                                                             float tol, int max_sweeps,
+                                                             const double* __restrict__ fro2, float zero_rel,
+                                                             JacobiCtl* ctl) {
+  __shared__ float part[16][64];
+  __shared__ float2 gm[64];
+  __shared__ float2 vm[64];
+  __shared__ float4 rot[4];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const unsigned nb = gridDim.x;
+  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
+  const float tiny = (float)fmax(fz, 1e-30);
+  const float conv = fmaxf(tol, 2e-4f);
+  int sweep = 0;
+  unsigned long long rotations = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float local_off = 0.f;
+    for (int r = 0; r < nblk - 1; ++r) {
+      for (int pb = blockIdx.x; pb < nblk / 2; pb += gridDim.x) {
+        int I, J;
+        round_robin_pair(r, pb, nblk, I, J);
+        int col[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int cj = (j < 4 ? I * 4 + j : J * 4 + j - 4);
+          col[j] = cj < n ? cj : -1;
+        }
+        // 1. Gram partials, 64 floats: |x_i|^2 (i < 8), then (re, im) of
+        // conj(x_i) x_j for the 28 pairs i < j; one row slot at a time
+        float v[64];
+#pragma unroll
+        for (int h = 0; h < 64; ++h) v[h] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < RPT; ++k) {
+          const int row = tid + 512 * k;
+          float2 x[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            x[j] = (col[j] >= 0 && row < m) ? G[(long long)col[j] * m + row] : float2{0.f, 0.f};
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = fmaf(x[i].x, x[i].x, fmaf(x[i].y, x[i].y, v[i]));
+          int e = 8;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = i + 1; j < 8; ++j) {
+              const float2 a = x[i], b = x[j];
+              v[e] = fmaf(a.x, b.x, fmaf(a.y, b.y, v[e]));
+              v[e + 1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, v[e + 1]));
+              e += 2;
+            }
+          }
+        }
+        // reduce-scatter over the five lane bits: 64 -> 2 values per lane;
+        // lane L ends with values 2 * (L reversed-bit-order position) .. + 1
+#pragma unroll
+        for (int bit = 4, half = 32; bit >= 0; --bit, half >>= 1) {
+          const bool up = (lane >> bit) & 1;
+#pragma unroll
+          for (int h = 0; h < half; ++h) {
+            const float send = up ? v[h] : v[half + h];
+            const float keep = up ? v[half + h] : v[h];
+            v[h] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << bit);
+          }
+        }
+        {
+          const int base = ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 +
+                           ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
+          part[w][base] = v[0];
+          part[w][base + 1] = v[1];
+        }
+        __syncthreads();
+        if (tid < 64) {
+          float sum = 0.f;
+#pragma unroll
+          for (int ww = 0; ww < 16; ++ww) sum += part[ww][tid];
+          float* g = reinterpret_cast<float*>(gm);
+          if (tid < 8) {
+            g[2 * (tid * 9)] = sum;
+            g[2 * (tid * 9) + 1] = 0.f;
+          } else {
+            int i, j;
+            pair_index((tid - 8) >> 1, i, j);
+            if (tid & 1) {
+              g[2 * (i * 8 + j) + 1] = sum;
+              g[2 * (j * 8 + i) + 1] = -sum;
+            } else {
+              g[2 * (i * 8 + j)] = sum;
+              g[2 * (j * 8 + i)] = sum;
+            }
+          }
+        } else if (tid >= 128 && tid < 192) {
+          const int e = tid - 128;
+          vm[e] = make_float2((e % 9) == 0 ? 1.f : 0.f, 0.f);
+        }
+        __syncthreads();
+        // 2. one cyclic Jacobi sweep on the Gram (warp 0)
+        if (w == 0) {
+          for (int st = 0; st < 7; ++st) {
+            if (lane < 4) {
+              int p, q;
+              round_robin_pair(st, lane, 8, p, q);
+              const float al = gm[p * 9].x, be = gm[q * 9].x;
+              const float2 g = gm[p * 8 + q];
+              const float gabs = sqrtf(g.x * g.x + g.y * g.y);
+              float4 rr = make_float4(1.f, 0.f, 1.f, 0.f);
+              if (al > tiny && be > tiny && gabs > tiny) {
+                const float rel = gabs / sqrtf(al * be);
+                if (rel > tol) {
+                  local_off = fmaxf(local_off, rel);
+                  ++rotations;
+                  const float zeta = (al - be) / (2.f * gabs);
+                  const float sg = zeta >= 0.f ? 1.f : -1.f;
+                  const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                  const float c = 1.f / sqrtf(1.f + t * t);
+                  rr = make_float4(c, c * t, g.x / gabs, -g.y / gabs);
+                }
+              }
+              rot[lane] = rr;
+            }
+            __syncwarp();
+            float2 ng[2], nv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int e = lane + 32 * u, i = e >> 3, j = e & 7;
+              int pi, pj, ki, kj;
+              bool fi, fj;
+              step_role(st, i, pi, ki, fi);
+              step_role(st, j, pj, kj, fj);
+              float2 ai, bi, aj, bj;
+              rot_coeffs(rot[ki], fi, ai, bi);
+              rot_coeffs(rot[kj], fj, aj, bj);
+              // G'_ij = conj(A_i) (G_ij A_j + G_i,pj B_j) + conj(B_i) (G_pi,j A_j + G_pi,pj B_j)
+              const float2 t1 = make_float2(cmulf(gm[i * 8 + j], aj).x + cmulf(gm[i * 8 + pj], bj).x,
+                                            cmulf(gm[i * 8 + j], aj).y + cmulf(gm[i * 8 + pj], bj).y);
+              const float2 t2 = make_float2(cmulf(gm[pi * 8 + j], aj).x + cmulf(gm[pi * 8 + pj], bj).x,
+                                            cmulf(gm[pi * 8 + j], aj).y + cmulf(gm[pi * 8 + pj], bj).y);
+              const float2 u1 = cmulcf(ai, t1), u2 = cmulcf(bi, t2);
+              ng[u] = make_float2(u1.x + u2.x, u1.y + u2.y);
+              const float2 v1 = cmulf(vm[i * 8 + j], aj), v2 = cmulf(vm[i * 8 + pj], bj);
+              nv[u] = make_float2(v1.x + v2.x, v1.y + v2.y);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              gm[lane + 32 * u] = ng[u];
+              vm[lane + 32 * u] = nv[u];
+            }
+            __syncwarp();
+          }
+        }
+        __syncthreads();
+        // 3. X <- X V (rows re-read: they are in L1)
+#pragma unroll 1
+        for (int k = 0; k < RPT; ++k) {
+          const int row = tid + 512 * k;
+          if (row >= m) break;
+          float2 x[8], y[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            x[j] = col[j] >= 0 ? G[(long long)col[j] * m + row] : float2{0.f, 0.f};
+            y[j] = make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 vv = vm[i * 8 + j];
+              y[j].x = fmaf(x[i].x, vv.x, fmaf(-x[i].y, vv.y, y[j].x));
+              y[j].y = fmaf(x[i].x, vv.y, fmaf(x[i].y, vv.x, y[j].y));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (col[j] >= 0) G[(long long)col[j] * m + row] = y[j];
+        }
+        __syncthreads();   // part, gm, vm are reused by the next pair of blocks
+      }
+      if (w == 0) {
+        float mx = local_off;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(mx));
+      }
+      local_off = 0.f;
+      if (!grid_barrier(ctl, nb)) {
+        if (rotations) atomicAdd(&ctl->rotations, rotations);
+        return;
+      }
+      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (!(off > conv)) { ++sweep; break; }
+  }
+  if (rotations) atomicAdd(&ctl->rotations, rotations);
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->sweeps = sweep;
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    if (sweep >= max_sweeps && off > conv && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
+  }
+}
+
 // ---- column norms, sort, truncation rank
 
 template <typename R>
@@ -856,6 +1113,11 @@ size_t jacobi_ctl_bytes() { return sizeof(JacobiCtl); }
 
 namespace {
 
+// complex64 Jacobi kernel for m <= 1024: 0 = warp-pair columns (jacobi_wp4),
+// 1 = Gram blocks (jacobi_gram); set by dmrgc_set_jacobi_kernel
+std::atomic<int> g_jacobi_variant{0};
+int jacobi_variant() { return g_jacobi_variant.load(std::memory_order_relaxed); }
+
 template <typename R>
 cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, const double* fro2,
                           double zero_rel, JacobiCtl* c, cudaStream_t st) {
@@ -867,11 +1129,18 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   void* fn;
   int threads = 128, blocks;
-  const bool wide = sizeof(R) == 4 && m <= 32 * 32 && n >= 16;
-  const bool blocked = !wide && sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
+  const bool gram = sizeof(R) == 4 && m <= 512 * 2 && n >= 16 && jacobi_variant() == 1;
+  const bool wide = !gram && sizeof(R) == 4 && m <= 32 * 32 && n >= 16;
+  const bool blocked = !gram && !wide && sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
   int nblk = 0;
   size_t dyn_smem = 0;
-  if (wide) {
+  if (gram) {
+    threads = 512;
+    nblk = (n + 3) / 4;
+    nblk += nblk & 1;
+    fn = (m <= 512) ? (void*)jacobi_gram_kernel<1> : (void*)jacobi_gram_kernel<2>;
+    blocks = nblk / 2;
+  } else if (wide) {
     threads = 256;
     nblk = (n + 3) / 4;
     nblk += nblk & 1;
@@ -1099,5 +1368,11 @@ extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, 
   if (gather_columns(G, m, n, tr.k, res, false, 0, U_out, fp64, st) != cudaSuccess) return DMRGC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return DMRGC_ECUDA;
   *k_out = tr.k;
+  return DMRGC_OK;
+}
+
+extern "C" dmrgc_status dmrgc_set_jacobi_kernel(int variant) {
+  if (variant < 0 || variant > 1) return DMRGC_EINVAL;
+  dmrgc::g_jacobi_variant.store(variant, std::memory_order_relaxed);
   return DMRGC_OK;
 }

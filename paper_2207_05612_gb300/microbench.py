@@ -3,7 +3,7 @@ seeded random inputs.  Also the small-case driver for profiler captures of a
 single kernel.
 
   python -m paper_2207_05612_gb300.microbench gemm --precision bf16x3 --m 65536 --n 1024 --k 512
-  python -m paper_2207_05612_gb300.microbench svd --precision fp32 --m 1024 --n 1024
+  python -m paper_2207_05612_gb300.microbench svd --precision fp32 --m 1024 --n 1024 [--jacobi gram]
 
 gemm: C = A B through dmrgc_test_gemm (host complex128 buffers in and out, so
 the wall time includes the transfers and the operand split); reports the wall
@@ -92,13 +92,17 @@ def main(argv=None) -> int:
     ap.add_argument("--k", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
+                    help="complex64 Jacobi kernel for m <= 1024")
     a = ap.parse_args(argv)
+    binding.dmrgc_set_jacobi_kernel(0 if a.jacobi == "wp4" else 1)
     prec = PREC[a.precision]
     if a.kernel == "gemm":
         out = bench_gemm(prec, a.m, a.n, a.k, a.reps, a.seed)
     else:
         out = bench_svd(prec, a.m, a.n, a.reps, a.seed)
     out["precision"] = a.precision
+    out["jacobi"] = a.jacobi
     print(json.dumps(out))
     return 0
 

@@ -83,3 +83,29 @@ def test_jacobi_rank_deficient_wide(prec):
     assert k == r
     tol = 1e-12 if prec == 0 else 3e-5
     assert np.abs(s[:r] - want[:r]).max() <= tol * want[0]
+
+
+@pytest.mark.parametrize("m,n", [(64, 48), (200, 130), (512, 512), (1000, 700), (1024, 1024), (37, 200)])
+def test_jacobi_gram_kernel_matches_lapack(m, n):
+    """The Gram-block Jacobi kernel (complex64, m <= 1024): singular values
+    against LAPACK, orthonormal kept vectors spanning the top subspace, ragged
+    sizes (n not a multiple of 8, m not of 512) included."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(m + 3 * n)
+    r = min(m, n)
+    u, _ = np.linalg.qr(_rand(rng, (m, r)))
+    v, _ = np.linalg.qr(_rand(rng, (n, r)))
+    sv = np.exp(-np.linspace(0, 5, r))
+    g = (u * sv) @ v.conj().T
+    chi = max(1, r // 2)
+    binding.dmrgc_set_jacobi_kernel(1)
+    try:
+        s, k, uk = binding.dmrgc_test_svd(3, g, chi, 2e-5)
+    finally:
+        binding.dmrgc_set_jacobi_kernel(0)
+    tol = 2e-5
+    assert np.abs(s[:r] - sv).max() <= tol * sv[0] * 10
+    assert k == chi
+    assert np.allclose(uk.conj().T @ uk, np.eye(k), atol=1e-4)
+    p_true = u[:, :k] @ u[:, :k].conj().T
+    assert np.abs(p_true @ uk - uk).max() < 1e-2
