@@ -65,8 +65,10 @@ typedef struct {
   int svd_mode;               /* truncated SVD of theta in the sweep:
                                  0 = one-sided Jacobi;
                                  1 = randomized range finder with a sketch of r + p columns,
-                                     r = the bond's current dimension, falling back to the
-                                     Jacobi SVD when the sketch fails its acceptance test;
+                                     r = the rank that held all but 1e-6 of the weight kept
+                                     at the bond's last update, tried when r + p is below
+                                     half the smaller side of theta, falling back to the
+                                     Jacobi SVD when the sketch fails its certificate;
                                  2 = the same with r predicted by the rank model
                                      (dmrgc_set_rank_model) */
   double sweep_rel_cutoff;    /* keep s_mu > cutoff * s_1 in the sweep SVD; <= 0: default
@@ -80,11 +82,10 @@ typedef struct {
   int rsvd_oversample;        /* p, extra sketch columns; <= 0: 8 */
   int rsvd_power_iters;       /* q, power iterations (each re-orthonormalised); 0..8
                                  (dmrgc_default_options: 1) */
-  double rsvd_tolerance;      /* tol of the sketch acceptance: accept when the weight of theta
-                                 outside the sketch is <= tol * f (the result is then within
-                                 tol of the optimal update), or, at a bond already updated in
-                                 this layer, when f >= (1 - tol) * the current partial
-                                 fidelity; <= 0: 1e-6 for FP64, 2e-5 for complex64 */
+  double rsvd_tolerance;      /* tol of the sketch certificate: accept when the weight the
+                                 optimum could hold beyond the sketch's f is <= tol * f (the
+                                 result is then within tol of the optimal update); <= 0: 1e-6
+                                 for FP64, 2e-5 for complex64 */
   int log_rank_records;       /* 1: log one rank-model record per full (Jacobi) SVD at a bond
                                  updated before (dmrgc_rank_records) */
 } dmrgc_options;

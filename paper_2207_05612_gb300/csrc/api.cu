@@ -60,7 +60,6 @@ struct dmrgc_ctx {
   DevBuf rs_om, rs_y, rs_q, rs_b, rs_h, rs_w, feat, mlp_w, mlp_out, lab;
   int layer_no = 0;
   std::vector<int> visit_layer;   // per bond: layer of the last update there (-1 none)
-  std::vector<int> rs_fail;       // per bond: layer in which a sketch was rejected
   std::vector<int> kprev;         // per bond: kept rank at the last update (0 = none)
   unsigned long long rs_ctr = 0;  // counter of the sketch random stream
   double rs_tol = 1e-6;
@@ -335,15 +334,19 @@ dmrgc_status form_theta(dmrgc_ctx* c, int i, int& mrow, int& ncol) {
 // Jacobi with the numerical-zero level, so rank-deficient sketches lose their
 // null directions instead of dividing by them.
 //
-// Acceptance (else the update falls back to the full Jacobi SVD):
-//  - certificate: theta^+ theta = B^+ B + (rest), both positive semidefinite,
-//    so by Ky Fan the best weight of k <= chi singular values of theta is at
-//    most that of B plus |theta|^2 - |B|^2.  With f the weight kept from B:
-//    if k = chi the optimum is at most f + |theta|^2 - |B|^2; if fewer were
-//    kept (the rest fell below the cut) at most |theta|^2.  Accept when that
-//    excess is at most tol * f: the result is within tol of the optimal update;
-//  - or, at a bond already updated in this layer, f >= (1 - tol) f_cur: the
-//    update keeps the partial fidelity the sweep already reached.
+// Acceptance (else the update falls back to the full Jacobi SVD), a
+// certificate: theta^+ theta = B^+ B + (rest), both positive semidefinite, so
+// by Ky Fan the best weight of k <= chi singular values of theta is at most
+// that of B plus |theta|^2 - |B|^2.  With f the weight kept from B: if k = chi
+// the optimum is at most f + |theta|^2 - |B|^2; if fewer were kept (the rest
+// fell below the cut) at most |theta|^2.  Accept when that excess is at most
+// tol * f: the result is then within tol of the optimal update.
+//
+// Sketch size: r + p with r the rank that held all but 1e-6 of the kept
+// weight at the bond's last update (svd_mode 1), or the rank model's
+// prediction of it (svd_mode 2).  The sketch is tried only when r + p is below
+// half the smaller side of theta: each orthonormalisation is a Jacobi on r + p
+// columns, so a larger sketch costs about as much as the full SVD.
 
 // orthonormal basis of the columns of W (column-major rows x cols): every
 // direction above the numerical-zero level, out row-major [rows][r]
@@ -431,12 +434,7 @@ dmrgc_status rsvd_try(dmrgc_ctx* c, int i, bool adj, int mrow, int ncol, int l, 
   // when fewer than chi values were kept, the sketch's own values below the cut
   const double tol = c->rs_tol;
   const double gap = (fro_theta - trh) + (kk < c->chi ? trh - ff : 0.0);
-  const bool cert = gap <= tol * ff;
-  const bool keeps = c->visit_layer[i] == c->layer_no && ff >= (1.0 - tol) * c->f_cur;
-  if (!(cert || keeps)) {
-    c->rs_fail[i] = c->layer_no;
-    return DMRGC_OK;
-  }
+  if (!(gap <= tol * ff)) return DMRGC_OK;
   accepted = true;
   c->stats.rsvd_accepted++;
   TRY(ensure(c, c->rs_w, (size_t)lq * kk * es));
@@ -483,8 +481,11 @@ dmrgc_status sketch_size(dmrgc_ctx* c, int i, int mrow, int ncol, int& l) {
   if (c->opt.svd_mode == 0 || nmin < 32) return DMRGC_OK;
   int r = 0;
   if (c->opt.svd_mode == 1) {
-    if (c->rs_fail[i] == c->layer_no) return DMRGC_OK;   // rejected here in this layer already
-    r = c->chiA[i + 1];                                   // the current bond dimension
+    if (c->kprev[i] <= 0) return DMRGC_OK;
+    int lab = 0;   // the rank the last update here needed (its spectrum's label)
+    CK(cudaMemcpyAsync(&lab, (const int*)c->lab.p + i, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    TRY(sync(c));
+    r = lab;
   } else {
     if (!c->mlp_ready || c->kprev[i] <= 0) return DMRGC_OK;
     float e[4];
@@ -502,7 +503,7 @@ dmrgc_status sketch_size(dmrgc_ctx* c, int i, int mrow, int ncol, int& l) {
     r = (int)std::ceil(std::exp2(std::min(std::max((double)y, 0.0), 20.0)));
   }
   const int want = r + c->rs_p;
-  if (want >= (int)(0.7 * nmin)) return DMRGC_OK;
+  if (2 * want >= nmin) return DMRGC_OK;
   l = std::max(want, 1);
   return DMRGC_OK;
 }
@@ -529,12 +530,15 @@ dmrgc_status record_end(dmrgc_ctx* c, int i, int k, bool full, const std::vector
     CK(spectrum_summary(c->tres.p, k, (float*)c->feat.p + 32 * (size_t)i, c->st));
     c->stats.kernel_launches++;
   }
-  if (full && !x.empty()) {
-    TRY(ensure(c, c->lab, 64));
-    CK(rank_label(c->tres.p, k, 1.0 - 1e-6, (int*)c->lab.p, c->st));
+  if (c->opt.svd_mode != 0 || c->opt.log_rank_records) {
+    // per bond: the rank holding all but 1e-6 of the kept weight
+    TRY(ensure(c, c->lab, sizeof(int) * (size_t)c->N));
+    CK(rank_label(c->tres.p, k, 1.0 - 1e-6, (int*)c->lab.p + i, c->st));
     c->stats.kernel_launches++;
+  }
+  if (full && !x.empty()) {
     int r = 0;
-    CK(cudaMemcpyAsync(&r, c->lab.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&r, (const int*)c->lab.p + i, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     TRY(sync(c));
     c->rec_x.insert(c->rec_x.end(), x.begin(), x.end());
     c->rec_y.push_back((float)std::log2((double)std::max(r, 1)));
@@ -959,7 +963,6 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
   c->L = EnvRef(); c->R = EnvRef();
   c->layer_no = 0;
   c->visit_layer.assign(n_qubits, -1);
-  c->rs_fail.assign(n_qubits, -1);
   c->kprev.assign(n_qubits, 0);
   c->rs_ctr = 0;
   c->rs_p = c->opt.rsvd_oversample > 0 ? c->opt.rsvd_oversample : 8;
