@@ -752,8 +752,7 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
 //     kernels' rotation (same zero level, threshold and formulas); the
 //     rotation is applied to the Gram on both sides and accumulated in V;
 //  3. every thread replaces its rows by X V.
-// Pairs inside a block are revisited every round; pairs across blocks meet
-// once per sweep of the block round-robin.  The sweep ends, like the column
+// Every pair of columns is rotated once per sweep, as in the column kernels.  The sweep ends, like the column
 // kernels, when its largest rotated |gamma| / sqrt(alpha beta) is below the
 // threshold.
 
@@ -765,16 +764,33 @@ __device__ __forceinline__ void pair_index(int e, int& i, int& j) {
   j = i + 1 + e;
 }
 
-// role of index x in step s of the 8-index round-robin: partner, first (p) or second (q)
+// Steps of the inner sweep on 8 indices (0-3: block I, 4-7: block J).  The
+// four cross steps pair every column of I with every column of J; the three
+// intra steps pair the columns inside each block (run in the first round of a
+// sweep only, as in the column kernels).  Entry: partner * 8 + pair * 2 + first.
+__constant__ unsigned char kGramStep[7][8] = {
+    // cross: (i, 4 + (i + s) % 4)
+    {4 * 8 + 0 * 2 + 1, 5 * 8 + 1 * 2 + 1, 6 * 8 + 2 * 2 + 1, 7 * 8 + 3 * 2 + 1,
+     0 * 8 + 0 * 2 + 0, 1 * 8 + 1 * 2 + 0, 2 * 8 + 2 * 2 + 0, 3 * 8 + 3 * 2 + 0},
+    {5 * 8 + 0 * 2 + 1, 6 * 8 + 1 * 2 + 1, 7 * 8 + 2 * 2 + 1, 4 * 8 + 3 * 2 + 1,
+     3 * 8 + 3 * 2 + 0, 0 * 8 + 0 * 2 + 0, 1 * 8 + 1 * 2 + 0, 2 * 8 + 2 * 2 + 0},
+    {6 * 8 + 0 * 2 + 1, 7 * 8 + 1 * 2 + 1, 4 * 8 + 2 * 2 + 1, 5 * 8 + 3 * 2 + 1,
+     2 * 8 + 2 * 2 + 0, 3 * 8 + 3 * 2 + 0, 0 * 8 + 0 * 2 + 0, 1 * 8 + 1 * 2 + 0},
+    {7 * 8 + 0 * 2 + 1, 4 * 8 + 1 * 2 + 1, 5 * 8 + 2 * 2 + 1, 6 * 8 + 3 * 2 + 1,
+     1 * 8 + 1 * 2 + 0, 2 * 8 + 2 * 2 + 0, 3 * 8 + 3 * 2 + 0, 0 * 8 + 0 * 2 + 0},
+    // intra: (0,1)(2,3)(4,5)(6,7); (0,2)(1,3)(4,6)(5,7); (0,3)(1,2)(4,7)(5,6)
+    {1 * 8 + 0 * 2 + 1, 0 * 8 + 0 * 2 + 0, 3 * 8 + 1 * 2 + 1, 2 * 8 + 1 * 2 + 0,
+     5 * 8 + 2 * 2 + 1, 4 * 8 + 2 * 2 + 0, 7 * 8 + 3 * 2 + 1, 6 * 8 + 3 * 2 + 0},
+    {2 * 8 + 0 * 2 + 1, 3 * 8 + 1 * 2 + 1, 0 * 8 + 0 * 2 + 0, 1 * 8 + 1 * 2 + 0,
+     6 * 8 + 2 * 2 + 1, 7 * 8 + 3 * 2 + 1, 4 * 8 + 2 * 2 + 0, 5 * 8 + 3 * 2 + 0},
+    {3 * 8 + 0 * 2 + 1, 2 * 8 + 1 * 2 + 1, 1 * 8 + 1 * 2 + 0, 0 * 8 + 0 * 2 + 0,
+     7 * 8 + 2 * 2 + 1, 6 * 8 + 3 * 2 + 1, 5 * 8 + 3 * 2 + 0, 4 * 8 + 2 * 2 + 0}};
+
 __device__ __forceinline__ void step_role(int s, int x, int& partner, int& pair, bool& first) {
-  partner = x; pair = 0; first = true;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    int a, b;
-    round_robin_pair(s, k, 8, a, b);
-    if (a == x) { partner = b; pair = k; first = true; }
-    if (b == x) { partner = a; pair = k; first = false; }
-  }
+  const int c = kGramStep[s][x];
+  partner = c >> 3;
+  pair = (c >> 1) & 3;
+  first = c & 1;
 }
 
 // R_{x x} (self) and R_{partner, x} (other) of the 2x2 rotation with
@@ -889,10 +905,17 @@ __global__ void __launch_bounds__(512, 1) jacobi_gram_kernel(float2* __restrict_
         __syncthreads();
         // 2. one cyclic Jacobi sweep on the Gram (warp 0)
         if (w == 0) {
-          for (int st = 0; st < 7; ++st) {
+          for (int st = (r == 0 ? 0 : 3); st < 7; ++st) {
+            const int sx = st < 3 ? st + 4 : st - 3;   // intra steps first in round 0
             if (lane < 4) {
-              int p, q;
-              round_robin_pair(st, lane, 8, p, q);
+              // pair `lane` of step sx: its first index p and partner q
+              int p = 0;
+#pragma unroll
+              for (int x = 0; x < 8; ++x) {
+                const int cx = kGramStep[sx][x];
+                if ((cx & 1) && ((cx >> 1) & 3) == lane) p = x;
+              }
+              const int q = kGramStep[sx][p] >> 3;
               const float al = gm[p * 9].x, be = gm[q * 9].x;
               const float2 g = gm[p * 8 + q];
               const float gabs = sqrtf(g.x * g.x + g.y * g.y);
@@ -918,8 +941,8 @@ __global__ void __launch_bounds__(512, 1) jacobi_gram_kernel(float2* __restrict_
               const int e = lane + 32 * u, i = e >> 3, j = e & 7;
               int pi, pj, ki, kj;
               bool fi, fj;
-              step_role(st, i, pi, ki, fi);
-              step_role(st, j, pj, kj, fj);
+              step_role(sx, i, pi, ki, fi);
+              step_role(sx, j, pj, kj, fj);
               float2 ai, bi, aj, bj;
               rot_coeffs(rot[ki], fi, ai, bi);
               rot_coeffs(rot[kj], fj, aj, bj);
@@ -1175,7 +1198,7 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   if (blocks < 1) blocks = 1;
   C2* g = reinterpret_cast<C2*>(G);
   R tl = (R)tol, zr = (R)zero_rel;
-  int mm = m, nn = n, npp = (wide || blocked) ? nblk : np, ms = max_sweeps;
+  int mm = m, nn = n, npp = (gram || wide || blocked) ? nblk : np, ms = max_sweeps;
   void* args[] = {&g, &mm, &nn, &npp, &tl, &ms, (void*)&fro2, &zr, &c};
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, dyn_smem, st);
 }
