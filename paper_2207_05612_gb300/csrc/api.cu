@@ -274,7 +274,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
                          void* W = nullptr, int chi_cap = -1) {
   if (!W) W = c->jw.p;
   if (chi_cap < 0) chi_cap = c->chi;
-  TRY(ensure(c, c->jctl, jacobi_ctl_bytes()));
+  TRY(ensure(c, c->jctl, jacobi_ctl_bytes(n)));
   TRY(ensure(c, c->tres, trunc_bytes(n)));
   TRY(ensure(c, c->scal, 64));
   double* fro2 = (double*)c->scal.p + 1;
@@ -289,7 +289,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
     c->stats.svd_launches += launches + 3;
     c->stats.kernel_launches += launches + 3;
   }
-  struct { int count, gen; unsigned off[2]; int err, sweeps; unsigned long long rot; } ctl{};
+  JacobiStatus ctl{};
   TruncResult tr{};
   CK(cudaMemcpyAsync(&ctl, c->jctl.p, sizeof(ctl), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(&tr, c->tres.p, sizeof(tr), cudaMemcpyDeviceToHost, c->st));
@@ -300,7 +300,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   if (tr.status != 0 || !std::isfinite(tr.f) || !(tr.f > 0))
     return fail(c, DMRGC_ENUMERIC, "truncated SVD met a zero or non-finite spectrum");
   c->stats.jacobi_sweeps += ctl.sweeps;
-  c->stats.svd_flops += (double)ctl.sweeps * 0.5 * n * (n - 1) * 16.0 * m + (double)ctl.rot * 14.0 * m;
+  c->stats.svd_flops += (double)ctl.sweeps * 0.5 * n * (n - 1) * 16.0 * m + (double)ctl.rotations * 14.0 * m;
   k = tr.k;
   f = tr.f;
   if (nnz) *nnz = tr.nnz;
@@ -1386,7 +1386,7 @@ dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int ch
   Scratch s;
   void* dG;
   if (upload_as(G, (long long)m * n, fp64, s, &dG) != cudaSuccess) return DMRGC_ECUDA;
-  void* ctl = s.get(jacobi_ctl_bytes());
+  void* ctl = s.get(jacobi_ctl_bytes(n));
   void* res = s.get(trunc_bytes(n));
   double* fro2 = (double*)s.get(sizeof(double));
   void* dU = s.get((size_t)(fp64 ? 16 : 8) * m * n);
@@ -1402,7 +1402,7 @@ dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int ch
       cudaSuccess)
     return DMRGC_ECUDA;
   TruncResult tr{};
-  struct { int count, gen; unsigned off[2]; int err, sweeps; unsigned long long rot; } cs{};
+  JacobiStatus cs{};
   if (cudaMemcpy(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
   if (cudaMemcpy(&cs, ctl, sizeof(cs), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
   if (cs.err == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;

@@ -67,8 +67,13 @@ cudaError_t gemm_tc(const GemmArgs& g, int precision, TcWork& w, int* err_dev, c
 // leading dimension m), in place: on return G = W = G0 V with mutually
 // orthogonal columns.  fro2: device pointer to |G|_F^2; columns with norm
 // below zero_rel*|G|_F are treated as zero.  ctl must point to device scratch
-// of jacobi_ctl_bytes().
-size_t jacobi_ctl_bytes();
+// of jacobi_ctl_bytes(n); it starts with a JacobiStatus the host may read.
+struct JacobiStatus {
+  int err;                        // 0, DMRGC_ETIMEOUT or DMRGC_ENOCONV
+  int sweeps;                     // sweeps executed
+  unsigned long long rotations;   // rotations applied
+};
+size_t jacobi_ctl_bytes(int n);
 cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
                                  const double* fro2, double zero_rel, void* ctl, cudaStream_t st,
                                  int* launches);

@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include <atomic>
+#include <cstddef>
 #include <mutex>
 
 #include "common.cuh"
@@ -26,13 +27,19 @@ namespace dmrgc {
 namespace {
 
 struct JacobiCtl {
+  int err;                // 0 ok, DMRGC_ETIMEOUT, DMRGC_ENOCONV   (JacobiStatus)
+  int sweeps;             // sweeps executed                         (JacobiStatus)
+  unsigned long long rotations;   // rotations applied (flop count)  (JacobiStatus)
   unsigned count;
   unsigned gen;
-  unsigned off_bits[2];   // float bits of the largest relative off-diagonal of a sweep
-  int err;                // 0 ok, DMRGC_ETIMEOUT, DMRGC_ENOCONV
-  int sweeps;             // sweeps executed
-  unsigned long long rotations;   // rotations applied (for the flop count)
+  unsigned off_bits[3];   // float bits of the largest relative off-diagonal of a sweep
+  unsigned pad[7];
+  // followed by one round counter per column block (jacobi_wp4_kernel)
 };
+static_assert(sizeof(JacobiCtl) == 64, "control block layout");
+static_assert(offsetof(JacobiCtl, rotations) == offsetof(JacobiStatus, rotations), "status prefix");
+
+__device__ __forceinline__ unsigned* block_rounds(JacobiCtl* c) { return reinterpret_cast<unsigned*>(c + 1); }
 
 constexpr unsigned long long kSpinLimit = 20000000ull;  // x ~64 ns = ~1.3 s
 
@@ -63,6 +70,39 @@ __device__ __forceinline__ bool grid_barrier(JacobiCtl* c, unsigned nblocks) {
   }
   __syncthreads();
   return *((volatile int*)&c->err) == 0;
+}
+
+// Wait (thread 0 polls, bounded) until blocks I and J have each completed
+// `need` rounds; then the CTA may read their columns.  false: error or timeout.
+__device__ __forceinline__ bool wait_rounds(JacobiCtl* c, const unsigned* done, int I, int J, unsigned need) {
+  if (threadIdx.x == 0) {
+    volatile const unsigned* di = done + I;
+    volatile const unsigned* dj = done + J;
+    volatile int* verr = &c->err;
+    unsigned long long it = 0;
+    while (*di < need || *dj < need) {
+      if (it > 4096) __nanosleep(64);
+      if (*verr != 0) break;
+      if (++it > kSpinLimit) {
+        atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&c->err) == 0;
+}
+
+// After the CTA stored blocks I and J: mark them `rounds` complete.
+__device__ __forceinline__ void publish_rounds(unsigned* done, int I, int J, unsigned rounds) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(done + I, rounds);
+    atomicExch(done + J, rounds);
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ void round_robin_pair(int r, int p, int np, int& a, int& b) {
@@ -677,14 +717,25 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
   const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
   const float tiny = (float)fmax(fz, 1e-30);
   const float conv = fmaxf(tol, 2e-4f);   // stop when a sweep's largest rotation is below conv
+  unsigned* done = block_rounds(ctl);      // rounds completed per column block
   int sweep = 0, buf = 0;
   unsigned long long rot = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    // slot of the sweep after next: every CTA read it at the end of sweep - 2,
+    // before passing the barrier that ended sweep - 1
+    if (blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) % 3] = 0u;
     float local_off = 0.f;
     for (int r = 0; r < nblk - 1; ++r) {
+      const unsigned need = (unsigned)sweep * (unsigned)(nblk - 1) + (unsigned)r;
       for (int pb = blockIdx.x; pb < nblk / 2; pb += gridDim.x) {
         int I, J;
         round_robin_pair(r, pb, nblk, I, J);
+        // the two blocks must have finished the previous round (point-to-point
+        // instead of a grid barrier: no CTA waits for the slowest one)
+        if (!wait_rounds(ctl, done, I, J, need)) {
+          if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+          return;
+        }
         const int col = (w < 4 ? I : J) * 4 + (w & 3);
         const bool valid = col < n;
         if (lane == 0) valid_all[w] = valid;
@@ -710,29 +761,27 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
             if (i < m) G[(long long)col * m + i] = x[e];
           }
         }
-        __syncthreads();   // valid_all and the buffers are reused by the next pair of blocks
+        publish_rounds(done, I, J, need + 1);   // ends with __syncthreads
       }
-      if (lane == 0) off_w[w] = local_off;
-      __syncthreads();
-      if (tid == 0) {
-        float mx = 0.f;
-        for (int i = 0; i < 8; ++i) mx = fmaxf(mx, off_w[i]);
-        if (mx > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(mx));
-      }
-      local_off = 0.f;
-      if (!grid_barrier(ctl, nb)) {
-        if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
-        return;
-      }
-      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
     }
-    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
+    if (lane == 0) off_w[w] = local_off;
+    __syncthreads();
+    if (tid == 0) {
+      float mx = 0.f;
+      for (int i = 0; i < 8; ++i) mx = fmaxf(mx, off_w[i]);
+      if (mx > 0.f) atomicMax(&ctl->off_bits[sweep % 3], __float_as_uint(mx));
+    }
+    if (!grid_barrier(ctl, nb)) {
+      if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
+      return;
+    }
+    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep % 3]));
     if (!(off > conv)) { ++sweep; break; }
   }
   if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
   if (blockIdx.x == 0 && tid == 0) {
     ctl->sweeps = sweep;
-    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
+    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) % 3]);
     if (sweep >= max_sweeps && off > conv && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
   }
 }
@@ -1132,7 +1181,7 @@ __global__ void gather_kernel(const typename cplx<R>::T* __restrict__ W, int m, 
 
 }  // namespace
 
-size_t jacobi_ctl_bytes() { return sizeof(JacobiCtl); }
+size_t jacobi_ctl_bytes(int n) { return sizeof(JacobiCtl) + sizeof(unsigned) * (size_t)((n + 3) / 4 + 2); }
 
 namespace {
 
@@ -1208,7 +1257,7 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
 cudaError_t jacobi_orthogonalize(void* G, int m, int n, bool fp64, double tol, int max_sweeps,
                                  const double* fro2, double zero_rel, void* ctl, cudaStream_t st,
                                  int* launches) {
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(JacobiCtl), st);
+  cudaError_t e = cudaMemsetAsync(ctl, 0, jacobi_ctl_bytes(n), st);
   if (e != cudaSuccess) return e;
   if (n < 2 || m < 1) return cudaSuccess;
   JacobiCtl* c = reinterpret_cast<JacobiCtl*>(ctl);
@@ -1354,7 +1403,8 @@ extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, 
                                           double rel_cut, double* s_out, int* k_out, void* U_out,
                                           void* stream) {
   using namespace dmrgc;
-  static_assert(256 + sizeof(TruncResult) + (sizeof(double) + sizeof(int)) * kNoAllocMaxCols + 64 <=
+  constexpr size_t kCtl = 4352;   // >= jacobi_ctl_bytes(kNoAllocMaxCols) = 4168
+  static_assert(kCtl + 256 + sizeof(TruncResult) + (sizeof(double) + sizeof(int)) * kNoAllocMaxCols + 64 <=
                     kNoAllocBytes,
                 "scratch array too small");
   if (precision < 0 || precision > 3 || m < 1 || m > (1 << 20) || n < 2 || n > kNoAllocMaxCols ||
@@ -1364,9 +1414,10 @@ extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned char* base = nullptr;
   if (scratch_for_current_device(&base) != cudaSuccess) return DMRGC_ECUDA;
-  void* ctl = base;                                   // JacobiCtl, cleared by the Jacobi launcher
-  double* fro2 = reinterpret_cast<double*>(base + 128);  // cleared by sum_abs2
-  void* res = base + 256;                             // TruncResult, s[n], perm[n]: written in full
+  if (jacobi_ctl_bytes(n) > kCtl) return DMRGC_EINVAL;
+  void* ctl = base;                                   // control block, cleared by the Jacobi launcher
+  double* fro2 = reinterpret_cast<double*>(base + kCtl);  // cleared by sum_abs2
+  void* res = base + kCtl + 256;                      // TruncResult, s[n], perm[n]: written in full
   const double eps = fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
   const double tol = 8.0 * eps * std::sqrt((double)m);
   const double zero_rel = fp64 ? 1e-13 : 1e-5;
@@ -1376,7 +1427,7 @@ extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, 
     return DMRGC_ECUDA;
   if (truncate_columns(G, m, n, fp64, chi, rel_cut, false, 0.0, fro2, zero_rel, res, st) != cudaSuccess)
     return DMRGC_ECUDA;
-  JacobiCtl hc{};
+  JacobiStatus hc{};
   TruncResult tr{};
   if (cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
