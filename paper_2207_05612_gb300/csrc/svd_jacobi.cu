@@ -629,6 +629,27 @@ __device__ __forceinline__ int wp4_partner(int w) {
   return w < 4 ? 4 + ((w + s) & 3) : ((w - 4 - s) & 3);
 }
 
+// Sums of four values over the warp, the same in every lane: reduce-scatter
+// over lane bits 4 and 3 (lane L keeps one of the four), sums over bits 2..0,
+// then each value is read from a lane that holds it (10 shuffles, not 20).
+__device__ __forceinline__ void warp_sum4(float& a, float& b, float& c, float& d) {
+  const int lane = threadIdx.x & 31;
+  const bool u4 = lane & 16, u3 = lane & 8;
+  float k0 = u4 ? c : a, k1 = u4 ? d : b;
+  const float s0 = u4 ? a : c, s1 = u4 ? b : d;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  float k = u3 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, u3 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  a = __shfl_sync(0xffffffffu, k, 0);
+  b = __shfl_sync(0xffffffffu, k, 8);
+  c = __shfl_sync(0xffffffffu, k, 16);
+  d = __shfl_sync(0xffffffffu, k, 24);
+}
+
 template <bool FIRST, int E>
 __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], bool ok, float tiny, float tol,
                                          float& local_off, unsigned long long& rot) {
@@ -646,10 +667,7 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
     p2 = __ffma2_rn(u, make_float2(v.y, v.x), p2);
   }
   float al = nu.x + nu.y, be = nv.x + nv.y, gr = p1.x + p1.y, gi = p2.x - p2.y;
-  al = warp_sum(al);
-  be = warp_sum(be);
-  gr = warp_sum(gr);
-  gi = warp_sum(gi);
+  warp_sum4(al, be, gr, gi);
   const float gabs = sqrtf(gr * gr + gi * gi);
   if (!ok || !(al > tiny) || !(be > tiny) || !(gabs > tiny)) return;
   const float rel = gabs / sqrtf(al * be);
@@ -683,21 +701,17 @@ __device__ __forceinline__ void wp4_subround(float2 (&x)[E], bool valid_me, cons
                                              unsigned long long& rot) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = wp4_partner<SUB>(w);
-  float2* base = sbuf + (long long)buf * 8 * m;
-  float2* mine = base + (long long)w * m;
-  const float2* theirs = base + (long long)p * m;
+  // columns are padded to 32 E rows in shared memory (rows >= m hold zeros in
+  // x and rotate as zeros), so the exchange needs no bounds checks
+  float2* base = sbuf + (long long)buf * 8 * 32 * E;
+  float2* mine = base + (long long)w * 32 * E;
+  const float2* theirs = base + (long long)p * 32 * E;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = lane + 32 * e;
-    if (i < m) mine[i] = x[e];
-  }
+  for (int e = 0; e < E; ++e) mine[lane + 32 * e] = x[e];
   __syncthreads();
   float2 y[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = lane + 32 * e;
-    y[e] = (i < m) ? theirs[i] : float2{0.f, 0.f};
-  }
+  for (int e = 0; e < E; ++e) y[e] = theirs[lane + 32 * e];
   buf ^= 1;   // the next sub-round writes the other buffer: no second barrier
   const bool ok = valid_me && valid_all[p];
   if (w < p) wp4_pair<true, E>(x, y, ok, tiny, tol, local_off, rot);
@@ -709,7 +723,7 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
                                                             float tol, int max_sweeps,
                                                             const double* __restrict__ fro2, float zero_rel,
                                                             JacobiCtl* ctl) {
-  extern __shared__ float2 sbuf[];          // 2 buffers x 8 columns x m
+  extern __shared__ float2 sbuf[];          // 2 buffers x 8 columns x 32 E
   __shared__ bool valid_all[8];
   __shared__ float off_w[8];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -1219,7 +1233,8 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
     if (m <= 32 * 8) fn = (void*)jacobi_wp4_kernel<8>;
     else if (m <= 32 * 16) fn = (void*)jacobi_wp4_kernel<16>;
     else fn = (void*)jacobi_wp4_kernel<32>;
-    dyn_smem = (size_t)2 * 8 * m * sizeof(float2);
+    const int E = m <= 32 * 8 ? 8 : (m <= 32 * 16 ? 16 : 32);
+    dyn_smem = (size_t)2 * 8 * 32 * E * sizeof(float2);
     cudaError_t ea = allow_dyn_smem(fn);
     if (ea != cudaSuccess) return ea;
     blocks = nblk / 2;
