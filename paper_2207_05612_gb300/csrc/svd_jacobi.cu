@@ -695,7 +695,7 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
   }
 }
 
-template <int SUB, int E>
+template <int SUB, int E, int VEC>
 __device__ __forceinline__ void wp4_subround(float2 (&x)[E], bool valid_me, const bool* valid_all, float2* sbuf,
                                              int m, int& buf, float tiny, float tol, float& local_off,
                                              unsigned long long& rot) {
@@ -706,19 +706,36 @@ __device__ __forceinline__ void wp4_subround(float2 (&x)[E], bool valid_me, cons
   float2* base = sbuf + (long long)buf * 8 * 32 * E;
   float2* mine = base + (long long)w * 32 * E;
   const float2* theirs = base + (long long)p * 32 * E;
-#pragma unroll
-  for (int e = 0; e < E; ++e) mine[lane + 32 * e] = x[e];
-  __syncthreads();
   float2 y[E];
+  if constexpr (VEC == 2) {   // 16-byte accesses: elements 2h, 2h+1 of a lane side by side
+    float4* mine4 = reinterpret_cast<float4*>(mine);
+    const float4* theirs4 = reinterpret_cast<const float4*>(theirs);
 #pragma unroll
-  for (int e = 0; e < E; ++e) y[e] = theirs[lane + 32 * e];
+    for (int h = 0; h < E / 2; ++h) mine4[lane + 32 * h] = make_float4(x[2 * h].x, x[2 * h].y, x[2 * h + 1].x, x[2 * h + 1].y);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < E / 2; ++h) {
+      const float4 v = theirs4[lane + 32 * h];
+      y[2 * h] = make_float2(v.x, v.y);
+      y[2 * h + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) mine[lane + 32 * e] = x[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = theirs[lane + 32 * e];
+  }
   buf ^= 1;   // the next sub-round writes the other buffer: no second barrier
   const bool ok = valid_me && valid_all[p];
   if (w < p) wp4_pair<true, E>(x, y, ok, tiny, tol, local_off, rot);
   else wp4_pair<false, E>(x, y, ok, tiny, tol, local_off, rot);
 }
 
-template <int E>
+// VEC = 2 (m even): a lane holds rows 64 h + 2 lane and 64 h + 2 lane + 1 as
+// elements 2h, 2h+1 and moves them with 16-byte loads and stores; VEC = 1: row
+// lane + 32 e as element e.
+template <int E, int VEC>
 __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__ G, int m, int n, int nblk,
                                                             float tol, int max_sweeps,
                                                             const double* __restrict__ fro2, float zero_rel,
@@ -754,25 +771,46 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
         const bool valid = col < n;
         if (lane == 0) valid_all[w] = valid;
         float2 x[E];
+        float2* gcol = G + (long long)col * m;
+        if constexpr (VEC == 2) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = lane + 32 * e;
-          x[e] = (valid && i < m) ? G[(long long)col * m + i] : float2{0.f, 0.f};
-        }
-        if (r == 0) {
-          wp4_subround<0, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-          wp4_subround<1, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-          wp4_subround<2, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-        }
-        wp4_subround<3, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-        wp4_subround<4, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-        wp4_subround<5, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-        wp4_subround<6, E>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
-        if (valid) {
+          for (int h = 0; h < E / 2; ++h) {
+            const int i = 64 * h + 2 * lane;   // m even: rows i, i + 1 both in range or both out
+            const float4 v = (valid && i < m) ? *reinterpret_cast<const float4*>(gcol + i)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[2 * h] = make_float2(v.x, v.y);
+            x[2 * h + 1] = make_float2(v.z, v.w);
+          }
+        } else {
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int i = lane + 32 * e;
-            if (i < m) G[(long long)col * m + i] = x[e];
+            x[e] = (valid && i < m) ? gcol[i] : float2{0.f, 0.f};
+          }
+        }
+        if (r == 0) {
+          wp4_subround<0, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+          wp4_subround<1, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+          wp4_subround<2, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        }
+        wp4_subround<3, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<4, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<5, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        wp4_subround<6, E, VEC>(x, valid, valid_all, sbuf, m, buf, tiny, tol, local_off, rot);
+        if (valid) {
+          if constexpr (VEC == 2) {
+#pragma unroll
+            for (int h = 0; h < E / 2; ++h) {
+              const int i = 64 * h + 2 * lane;
+              if (i < m)
+                *reinterpret_cast<float4*>(gcol + i) = make_float4(x[2 * h].x, x[2 * h].y, x[2 * h + 1].x, x[2 * h + 1].y);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int i = lane + 32 * e;
+              if (i < m) gcol[i] = x[e];
+            }
           }
         }
         publish_rounds(done, I, J, need + 1);   // ends with __syncthreads
@@ -1230,9 +1268,11 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
     threads = 256;
     nblk = (n + 3) / 4;
     nblk += nblk & 1;
-    if (m <= 32 * 8) fn = (void*)jacobi_wp4_kernel<8>;
-    else if (m <= 32 * 16) fn = (void*)jacobi_wp4_kernel<16>;
-    else fn = (void*)jacobi_wp4_kernel<32>;
+    // 16-byte column accesses need an even m (column starts then stay 16-byte aligned)
+    const bool v2 = (m % 2) == 0 && (reinterpret_cast<uintptr_t>(G) % 16) == 0;
+    if (m <= 32 * 8) fn = v2 ? (void*)jacobi_wp4_kernel<8, 2> : (void*)jacobi_wp4_kernel<8, 1>;
+    else if (m <= 32 * 16) fn = v2 ? (void*)jacobi_wp4_kernel<16, 2> : (void*)jacobi_wp4_kernel<16, 1>;
+    else fn = v2 ? (void*)jacobi_wp4_kernel<32, 2> : (void*)jacobi_wp4_kernel<32, 1>;
     const int E = m <= 32 * 8 ? 8 : (m <= 32 * 16 ? 16 : 32);
     dyn_smem = (size_t)2 * 8 * 32 * E * sizeof(float2);
     cudaError_t ea = allow_dyn_smem(fn);
