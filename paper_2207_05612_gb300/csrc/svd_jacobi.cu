@@ -682,16 +682,16 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
   const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float c = 1.f / sqrtf(1.f + t * t);
   const float sn = c * t;
-  const float2 E2{er, er}, EI{-ei, ei};
-  const float2 CC{c, c}, SS{sn, sn}, NS{-sn, -sn};
+  // first: u' = c u - s e^{-i phi} v;  second: v' = s u + c e^{-i phi} v.
+  // With b = (-s or c) e^{-i phi} = (br, bi):  b v = (br vx - bi vy, br vy + bi vx)
+  const float a = FIRST ? c : sn;
+  const float br = (FIRST ? -sn : c) * er, bi = (FIRST ? -sn : c) * ei;
+  const float2 AA{a, a}, BR{br, br}, BI{-bi, bi};
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const float2 u = FIRST ? x[e] : y[e];
     const float2 v = FIRST ? y[e] : x[e];
-    // ve = v e^{-i phi} = (vx er - vy ei, vy er + vx ei)
-    const float2 ve = __ffma2_rn(make_float2(v.y, v.x), EI, __fmul2_rn(v, E2));
-    // first: c u - s ve ; second: s u + c ve
-    x[e] = FIRST ? __ffma2_rn(CC, u, __fmul2_rn(NS, ve)) : __ffma2_rn(SS, u, __fmul2_rn(CC, ve));
+    x[e] = __ffma2_rn(AA, u, __ffma2_rn(BR, v, __fmul2_rn(BI, make_float2(v.y, v.x))));
   }
 }
 
