@@ -38,6 +38,15 @@ if ROOT not in sys.path:
 
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "fp32": 3}
 DTYPE_NAME = {"fp64": "c128-f64", "bf16x3": "c64-bf16x3", "tf32x3": "c64-tf32x3", "fp32": "c64-f32"}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of each kernel at the shape that dominates the bench (summaries
+# in profiles/).  Only reported while the bench runs that kernel variant.
+NCU_TRAFFIC = {
+    "jacobi_wp4": {"bytes": 10.76e6, "launch": "1024 x 1024 complex64 (saturated bond, chi = 512)",
+                   "profile": "profiles/jacobi_wp4_1024x1024_fp32.md"},
+    "tc_gemm_bf16x3": {"bytes": 760.07e6, "launch": "M 65536, N 1024, K 512",
+                       "profile": "profiles/tc_gemm_65536x1024x512_bf16x3.md"},
+}
 FP32_LANES_PER_SM = 128
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (CUDA cores and tensor cores alike)
 N_SMS = 152
@@ -354,6 +363,15 @@ def main(argv=None):
                 "peak": spk, "unit": "TFLOP/s", "frac": svd_ach / spk, "traffic": None,
                 "peak_note": "CUDA-core FMA peak: 152 SMs x 128 FP32 lanes x 2 x sampled SM clock"
                              if not fp64 else "nominal FP64 1.25 TFLOP/s x sampled/max SM clock"}
+    if args.precision == "bf16x3":
+        t = NCU_TRAFFIC["tc_gemm_bf16x3"]
+        roof_gemm["traffic"] = t["bytes"]
+        roof_gemm["traffic_note"] = f"ncu, one launch of {t['launch']} ({t['profile']})"
+    if not fp64 and args.jacobi == "wp4":
+        t = NCU_TRAFFIC["jacobi_wp4"]
+        roof_svd["traffic"] = t["bytes"]
+        roof_svd["traffic_note"] = (f"ncu, one launch of {t['launch']} ({t['profile']}); "
+                                    "achieved is the class aggregate over all launch sizes")
     roof = roof_gemm if st["gemm_ms"] >= st["svd_ms"] else roof_svd
     roof_other = roof_svd if roof is roof_gemm else roof_gemm
     cpu = None
