@@ -747,7 +747,10 @@ __global__ void __launch_bounds__(256, 1) jacobi_wp4_kernel(float2* __restrict__
   const unsigned nb = gridDim.x;
   const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
   const float tiny = (float)fmax(fz, 1e-30);
-  const float conv = fmaxf(tol, 2e-4f);   // stop when a sweep's largest rotation is below conv
+  // stop after a sweep whose largest rotation is below conv: the columns are
+  // then orthogonal to about conv^2 (the sweep's rotations move the pairs
+  // rotated earlier in it only at second order)
+  const float conv = fmaxf(tol, 2e-3f);
   unsigned* done = block_rounds(ctl);      // rounds completed per column block
   int sweep = 0, buf = 0;
   unsigned long long rot = 0;
