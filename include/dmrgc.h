@@ -76,7 +76,7 @@ typedef struct {
   double zip_rel_cutoff;      /* same for the truncating steps of the zip-up guess; <= 0:
                                  default (1e-5 for FP64, 4e-3 for the complex64 modes) */
   int max_jacobi_sweeps;      /* <= 0: default 40 */
-  unsigned long long seed;    /* reserved */
+  unsigned long long seed;    /* seed of the randomized SVD sketches (SplitMix64 counter stream) */
   void* cuda_stream;          /* cudaStream_t to launch on; NULL = default stream */
   int timing;                 /* 1: record CUDA-event time per kernel class (dmrgc_stats) */
   int rsvd_oversample;        /* p, extra sketch columns; <= 0: 8 */
