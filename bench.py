@@ -206,7 +206,8 @@ def run_ours(args, world, rank, local):
     circ = sc.random_circuit(rows, cols, cycles, seed=args.seed + rank)
     stream = torch.cuda.current_stream()
     prec = PRECISIONS[args.precision]
-    ctx = Context(rows, cols, args.chi, precision=prec, timing=True, stream=stream.cuda_stream)
+    ctx = Context(rows, cols, args.chi, precision=prec, timing=True, stream=stream.cuda_stream,
+                  mpo_compress=args.mpo_compress)
     packed = [binding.pack_gates(l) for l in circ.layers[:args.warmup]]
     bits = sc.random_bitstrings(n, 1024, seed=7)
     upd_per_step = 2 * (n - 1)
@@ -276,6 +277,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
                     help="complex64 Jacobi kernel for m <= 1024")
+    ap.add_argument("--mpo-compress", type=int, default=0, choices=[0, 1],
+                    help="1: lossless compression of each layer MPO before the guess")
     ap.add_argument("--records", type=int, default=20000, help="learned: training records to log")
     ap.add_argument("--eval-layers", type=int, default=4, help="learned: layers of the random circuit to run")
     ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned"],
@@ -307,6 +310,7 @@ def main(argv=None):
               "cycles_per_step": 2, "sweeps_per_step": 2,
               "updates_per_step": 2 * (args.rows * args.cols - 1),
               "jacobi_kernel": args.jacobi,
+              "mpo": "compressed (operator Schmidt ranks)" if args.mpo_compress else "product of gate Schmidt ranks",
               "l2": "inputs larger than L2 (environment caches of GBs), no flush"}
 
     if args.impl == "reference":
@@ -535,7 +539,8 @@ def learned_report(args):
     t_train = time.perf_counter() - t1
 
     def run(circ, chi, mode, layers):
-        ctx = Context(circ.rows, circ.cols, chi, precision=prec, timing=True, svd_mode=mode)
+        ctx = Context(circ.rows, circ.cols, chi, precision=prec, timing=True, svd_mode=mode,
+                      mpo_compress=args.mpo_compress)
         if mode == 2:
             ctx.set_rank_model(params)
         torch.cuda.synchronize()

@@ -88,6 +88,10 @@ typedef struct {
                                  for FP64, 2e-5 for complex64 */
   int log_rank_records;       /* 1: log one rank-model record per full (Jacobi) SVD at a bond
                                  updated before (dmrgc_rank_records) */
+  int mpo_compress;           /* 1: reduce each layer MPO's bonds to the operator Schmidt ranks
+                                 (Jacobi SVD of the site tensors, two passes, cut at the
+                                 sweep cutoff); 0 (default): the bond is the product of the
+                                 straddling gates' Schmidt ranks */
 } dmrgc_options;
 
 typedef struct {

@@ -36,7 +36,8 @@ class Options(C.Structure):
                 ("max_jacobi_sweeps", C.c_int), ("seed", C.c_ulonglong),
                 ("cuda_stream", C.c_void_p), ("timing", C.c_int),
                 ("rsvd_oversample", C.c_int), ("rsvd_power_iters", C.c_int),
-                ("rsvd_tolerance", C.c_double), ("log_rank_records", C.c_int)]
+                ("rsvd_tolerance", C.c_double), ("log_rank_records", C.c_int),
+                ("mpo_compress", C.c_int)]
 
 
 class Gate(C.Structure):

@@ -51,6 +51,7 @@ struct dmrgc_ctx {
   int max_jsweeps = 40;
   std::vector<int> order, site_of;
   std::vector<DevBuf> A, B, Wx, Wy, XY, E;
+  std::vector<DevBuf> Wc;   // layer MPO in [w_in][s][t][w_out] while it is compressed
   std::vector<int> chiA, chiB, D;     // N+1 entries each
   std::vector<char> xyk;
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
@@ -787,6 +788,122 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
 
 // ---- layer MPO plan
 
+// Lossless compression of the layer MPO: its bonds are reduced to the operator
+// Schmidt ranks of the layer across each cut (the built bond is the product of
+// the straddling gates' Schmidt ranks, which over-counts where gates share
+// qubits).  Site tensors are taken as matrices, factored by the one-sided
+// Jacobi SVD and cut at the sweep's relative cutoff (1e-12 in FP64, 2e-5 in
+// complex64) and the numerical-zero level; the singular values themselves
+// stay in the neighbouring tensor, so the product of the tensors does not
+// change beyond that cut.
+//  left to right:  W_i = Q R with orthonormal columns Q,  W_{i+1} <- R W_{i+1};
+//  right to left:  W_i = L Q' with orthonormal rows Q',  W_{i-1} <- W_{i-1} L.
+// After the first pass the left part is an isometry, so the second pass sees
+// the true operator Schmidt values.  A cut at full rank is left as it is.
+dmrgc_status compress_mpo(dmrgc_ctx* c) {
+  const int N = c->N;
+  const size_t es = c->esz;
+  if ((int)c->Wc.size() < N) c->Wc.resize(N);
+  for (int i = 0; i < N; ++i) {   // Wy[s][w_in][w_out][t] -> Wc[w_in][s][t][w_out]
+    const int dims[4] = {2, c->D[i], c->D[i + 1], 2}, perm[4] = {1, 0, 3, 2};
+    TRY(ensure(c, c->Wc[i], (size_t)4 * c->D[i] * c->D[i + 1] * es));
+    Span sp(c, TC_MPO);
+    CK(permute4(c->Wy[i].p, dims, perm, c->Wc[i].p, c->fp64, c->st));
+    c->stats.kernel_launches++;
+  }
+  auto replace = [&](DevBuf& dst, const DevBuf& src, size_t bytes) -> dmrgc_status {
+    TRY(ensure(c, dst, bytes));
+    CK(cudaMemcpyAsync(dst.p, src.p, bytes, cudaMemcpyDeviceToDevice, c->st));
+    return DMRGC_OK;
+  };
+  for (int i = 0; i + 1 < N; ++i) {
+    const int dl = c->D[i], dr = c->D[i + 1], dr2 = c->D[i + 2], rows = 4 * dl;
+    if (dr == 1) continue;
+    TRY(ensure(c, c->jw, (size_t)rows * dr * es));
+    {
+      Span sp(c, TC_OTHER);
+      CK(copy_transpose(c->Wc[i].p, rows, dr, false, c->jw.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    int k = 0, nnz = 0;
+    double f = 0;
+    TRY(svd_columns(c, rows, dr, c->sweep_cut, false, 0.0, k, f, &nnz, nullptr, c->jw.p, dr));
+    if (k >= dr) continue;
+    TRY(ensure(c, c->T, (size_t)rows * k * es));
+    {
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, rows, dr, k, c->tres.p, false, 0, c->T.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(ensure(c, c->envL, (size_t)k * dr * es));
+    GemmArgs g;   // R = Q^+ W_i  [k][dr]
+    g.M = k; g.N = dr; g.K = rows;
+    g.A = c->T.p; g.lda = k; g.opA = OP_C;
+    g.B = c->Wc[i].p; g.ldb = dr; g.opB = OP_N;
+    g.C = c->envL.p; g.ldc = dr;
+    TRY(gemm(c, g));
+    TRY(ensure(c, c->envR, (size_t)k * 4 * dr2 * es));
+    GemmArgs h;   // W_{i+1} <- R W_{i+1}  [k][4 dr2]
+    h.M = k; h.N = 4 * dr2; h.K = dr;
+    h.A = c->envL.p; h.lda = dr; h.opA = OP_N;
+    h.B = c->Wc[i + 1].p; h.ldb = 4 * dr2; h.opB = OP_N;
+    h.C = c->envR.p; h.ldc = 4 * dr2;
+    TRY(gemm(c, h));
+    TRY(replace(c->Wc[i + 1], c->envR, (size_t)k * 4 * dr2 * es));
+    TRY(replace(c->Wc[i], c->T, (size_t)rows * k * es));
+    c->D[i + 1] = k;
+  }
+  for (int i = N - 1; i >= 1; --i) {
+    const int dl = c->D[i], dr = c->D[i + 1], dl2 = c->D[i - 1], cols = 4 * dr;
+    if (dl == 1) continue;
+    TRY(ensure(c, c->jw, (size_t)dl * cols * es));
+    {
+      Span sp(c, TC_OTHER);   // columns of W_i^+ (column-major == conj(W_i) row-major)
+      CK(copy_conj(c->Wc[i].p, (long long)dl * cols, c->jw.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    int k = 0, nnz = 0;
+    double f = 0;
+    TRY(svd_columns(c, cols, dl, c->sweep_cut, false, 0.0, k, f, &nnz, nullptr, c->jw.p, dl));
+    if (k >= dl) continue;
+    TRY(ensure(c, c->T, (size_t)k * cols * es));
+    {
+      Span sp(c, TC_SVD);   // Q' [k][cols], orthonormal rows spanning the row space of W_i
+      CK(gather_columns(c->jw.p, cols, dl, k, c->tres.p, false, 2, c->T.p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(ensure(c, c->envL, (size_t)dl * k * es));
+    GemmArgs g;   // L = W_i Q'^+  [dl][k]
+    g.M = dl; g.N = k; g.K = cols;
+    g.A = c->Wc[i].p; g.lda = cols; g.opA = OP_N;
+    g.B = c->T.p; g.ldb = cols; g.opB = OP_C;
+    g.C = c->envL.p; g.ldc = k;
+    TRY(gemm(c, g));
+    TRY(ensure(c, c->envR, (size_t)4 * dl2 * k * es));
+    GemmArgs h;   // W_{i-1} <- W_{i-1} L  [4 dl2][k]
+    h.M = 4 * dl2; h.N = k; h.K = dl;
+    h.A = c->Wc[i - 1].p; h.lda = dl; h.opA = OP_N;
+    h.B = c->envL.p; h.ldb = k; h.opB = OP_N;
+    h.C = c->envR.p; h.ldc = k;
+    TRY(gemm(c, h));
+    TRY(replace(c->Wc[i - 1], c->envR, (size_t)4 * dl2 * k * es));
+    TRY(replace(c->Wc[i], c->T, (size_t)k * cols * es));
+    c->D[i] = k;
+  }
+  for (int i = 0; i < N; ++i) {   // Wc -> Wx[s][w_out][w_in][t], Wy[s][w_in][w_out][t]
+    const int dims[4] = {c->D[i], 2, 2, c->D[i + 1]};
+    const int px[4] = {1, 3, 0, 2}, py[4] = {1, 0, 3, 2};
+    const size_t bytes = (size_t)4 * c->D[i] * c->D[i + 1] * es;
+    TRY(ensure(c, c->Wx[i], bytes));
+    TRY(ensure(c, c->Wy[i], bytes));
+    Span sp(c, TC_MPO);
+    CK(permute4(c->Wc[i].p, dims, px, c->Wx[i].p, c->fp64, c->st));
+    CK(permute4(c->Wc[i].p, dims, py, c->Wy[i].p, c->fp64, c->st));
+    c->stats.kernel_launches += 2;
+  }
+  return DMRGC_OK;
+}
+
 dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
   const int N = c->N;
   std::vector<GateDev> gd(n_gates);
@@ -884,6 +1001,7 @@ dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
                       c->fp64, c->st));
     c->stats.kernel_launches++;
   }
+  if (c->opt.mpo_compress) TRY(compress_mpo(c));
   return DMRGC_OK;
 }
 
@@ -891,7 +1009,7 @@ dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
 
 dmrgc_ctx::~dmrgc_ctx() {
   auto fr = [](DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; };
-  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E})
+  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &Wc})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
                     &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr})
@@ -956,7 +1074,7 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
     }
   c->site_of.assign(n_qubits, 0);
   for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
-  for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E})
+  for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E, &c->Wc})
     if ((int)v->size() < n_qubits) v->resize(n_qubits);
   c->xyk.assign(n_qubits, 0);
   c->chiA.assign(n_qubits + 1, 1); c->chiB.assign(n_qubits + 1, 1); c->D.assign(n_qubits + 1, 1);

@@ -159,6 +159,8 @@ cudaError_t allow_dyn_smem(const void* fn);
 cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void* dst, bool fp64,
                            cudaStream_t st);   // dst[c*rows + r] = op(src[r*cols + c])
 cudaError_t copy_conj(const void* src, long long n, void* dst, bool fp64, cudaStream_t st);
+// 4-index transpose of a complex tensor: dims are the input's, out axis k is in axis perm[k]
+cudaError_t permute4(const void* src, const int* dims, const int* perm, void* dst, bool fp64, cudaStream_t st);
 cudaError_t permute_phys_first(const void* src, int a, int b, void* dst, bool fp64,
                                cudaStream_t st);  // [a][2][b] -> [2][a][b]
 cudaError_t set_identity(void* dst, int n, bool fp64, cudaStream_t st);  // n x n

@@ -185,6 +185,39 @@ cudaError_t copy_transpose(const void* src, int rows, int cols, bool conj, void*
   return cudaGetLastError();
 }
 
+namespace {
+
+// out[o0][o1][o2][o3] = in[...], out axis k = in axis p[k]
+template <typename C2>
+__global__ void permute4_kernel(const C2* __restrict__ in, int4 dims, int4 perm, C2* __restrict__ out, long long n) {
+  const int d[4] = {dims.x, dims.y, dims.z, dims.w};
+  const int p[4] = {perm.x, perm.y, perm.z, perm.w};
+  long long stride_in[4];
+  stride_in[3] = 1;
+  for (int k = 2; k >= 0; --k) stride_in[k] = stride_in[k + 1] * d[k + 1];
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    long long rem = o, src = 0;
+    for (int k = 3; k >= 0; --k) {
+      const int dk = d[p[k]];
+      src += (rem % dk) * stride_in[p[k]];
+      rem /= dk;
+    }
+    out[o] = in[src];
+  }
+}
+
+}  // namespace
+
+cudaError_t permute4(const void* src, const int* dims, const int* perm, void* dst, bool fp64, cudaStream_t st) {
+  const long long n = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (n <= 0) return cudaSuccess;
+  const int4 d = make_int4(dims[0], dims[1], dims[2], dims[3]);
+  const int4 p = make_int4(perm[0], perm[1], perm[2], perm[3]);
+  if (fp64) permute4_kernel<<<blocks_for(n), 256, 0, st>>>((const double2*)src, d, p, (double2*)dst, n);
+  else permute4_kernel<<<blocks_for(n), 256, 0, st>>>((const float2*)src, d, p, (float2*)dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t copy_conj(const void* src, long long n, void* dst, bool fp64, cudaStream_t st) {
   if (fp64) conj_kernel<<<blocks_for(n), 256, 0, st>>>((const double2*)src, n, (double2*)dst);
   else conj_kernel<<<blocks_for(n), 256, 0, st>>>((const float2*)src, n, (float2*)dst);

@@ -262,3 +262,35 @@ def test_qaoa_sampled_cut_value(prec, chi):
     cut = np.sum(smp[:, e[:, 0]] != smp[:, e[:, 1]], axis=1)
     assert abs(cut.mean() - exp_c) < 4 * cut.std() / np.sqrt(len(cut)) + 1e-9
 
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 2e-4)])
+def test_mpo_compression_keeps_the_layer(prec, tol):
+    """options.mpo_compress: the layer MPO's bonds shrink to the operator
+    Schmidt ranks the oracle's lossless compression finds (FP64: equal; the
+    complex64 cut may drop a value the FP64 cut keeps), and in the exact
+    regime every amplitude still matches the statevector."""
+    from paper_2207_05612_gb300 import Context
+    from oracle import mpo as om
+    circ = sc.random_circuit(3, 4, 8, seed=2)
+    order = om.snake_order(3, 4)
+    ctx = Context(3, 4, 64, precision=prec, mpo_compress=1)
+    shrunk = False
+    for layer in circ.layers:
+        ctx.apply_layer(layer)
+        _, dmpo = ctx.bond_dims()
+        want = [w.shape[3] for w in om.layer_mpo(layer, order, compress=True)][:-1]
+        naive = [w.shape[3] for w in om.layer_mpo(layer, order, compress=False)][:-1]
+        if prec == 0:
+            assert dmpo == want, (dmpo, want)
+        else:
+            assert all(a <= b for a, b in zip(dmpo, want))
+        shrunk |= sum(dmpo) < sum(naive)
+        ctx.sweep(2)
+    assert shrunk
+    exact = sv.run(12, circ.layers)[-1]
+    bits = all_bitstrings(12)
+    assert np.abs(ctx.amplitude(bits) - sv.amplitudes(exact, bits)).max() < tol
+    lf, _ = ctx.fidelity()
+    assert abs(lf) < (1e-10 if prec == 0 else 1e-4)
+    ctx.close()
