@@ -4,7 +4,8 @@ Workload (N=1): 54 qubits on a 6x9 grid, Sycamore-like random circuit
 (sqrt(X/Y/W) + fSim(pi/2, pi/6), staggered ABCD-CDAB pattern), K = 2 cycles per
 compression step, chi = 512, 2 sweeps per step (2(N-1) = 106 two-site updates).
 One benchmark step = one compression step of the whole hot path: layer-MPO
-build, zip-up guess, 106 updates (theta, truncated SVD, environments).  The
+build and lossless compression, zip-up guess, 106 updates (theta, truncated
+SVD, environments).  The
 first --warmup steps grow the bond dimension to chi; the next --steps are timed.
 
 value: updates/s from CUDA events on the library's stream (gate records already
@@ -277,8 +278,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
                     help="complex64 Jacobi kernel for m <= 1024")
-    ap.add_argument("--mpo-compress", type=int, default=0, choices=[0, 1],
-                    help="1: lossless compression of each layer MPO before the guess")
+    ap.add_argument("--mpo-compress", type=int, default=1, choices=[0, 1],
+                    help="1 (default): lossless compression of each layer MPO before the guess; "
+                         "0: the bond is the product of the straddling gates' Schmidt ranks")
     ap.add_argument("--records", type=int, default=20000, help="learned: training records to log")
     ap.add_argument("--eval-layers", type=int, default=4, help="learned: layers of the random circuit to run")
     ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned"],
