@@ -263,8 +263,9 @@ dmrgc_status dmrgc_mlp_predict(const float* params, const float* x, int n, int b
  * every instance it takes from the shared queue (its device buffers are kept,
  * so allocation stops once a worker has seen its largest instance); instances
  * of different size and bond dimension run concurrently on the streams.
- * Options (precision, cutoffs) apply to all; options.cuda_stream is ignored;
- * svd_mode 2 (which needs a rank model per context) returns DMRGC_EINVAL.
+ * Options (precision, cutoffs) apply to all; options.cuda_stream is ignored.
+ * rank_model (host, DMRGC_MLP_PARAMS floats, or NULL) is loaded into every
+ * worker's context; svd_mode 2 without it returns DMRGC_EINVAL.
  * For each item the caller fills the inputs; the call fills the outputs. */
 typedef struct {
   int rows, cols;            /* grid of this instance (n_qubits = rows*cols) */
@@ -282,7 +283,7 @@ typedef struct {
 } dmrgc_batch_item;
 
 dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, const dmrgc_options* opt,
-                             double* wall_seconds);
+                             const float* rank_model, double* wall_seconds);
 
 /* Truncated SVD of a device matrix that allocates no memory at all.
  *

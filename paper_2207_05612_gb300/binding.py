@@ -97,7 +97,7 @@ def lib():
                                      C.c_void_p, P(C.c_int), C.c_void_p]
         L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
-        L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), P(C.c_double)]
+        L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), C.c_void_p, P(C.c_double)]
         L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
         fp = C.c_void_p
         L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
@@ -280,12 +280,16 @@ def pack_batch(instances):
     return items, keep
 
 
-def dmrgc_batch_run(items, count: int, n_workers: int, options: Options | None = None) -> float:
+def dmrgc_batch_run(items, count: int, n_workers: int, options: Options | None = None,
+                    rank_model: np.ndarray | None = None) -> float:
     """Runs `count` packed instances on `n_workers` streams; fills the items'
-    outputs and returns the wall time in seconds."""
+    outputs and returns the wall time in seconds.  rank_model: parameters for
+    svd_mode 2 (loaded into every worker's context)."""
     wall = C.c_double()
     opt = options if options is not None else dmrgc_default_options()
-    _check(lib().dmrgc_batch_run(items, count, n_workers, C.byref(opt), C.byref(wall)))
+    model = None if rank_model is None else _f32(rank_model, (MLP_PARAMS,))
+    _check(lib().dmrgc_batch_run(items, count, n_workers, C.byref(opt),
+                                 None if model is None else model.ctypes.data, C.byref(wall)))
     return wall.value
 
 

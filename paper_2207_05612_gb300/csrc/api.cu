@@ -1150,7 +1150,7 @@ dmrgc_status dmrgc_rank_records(dmrgc_ctx* c, float* features, float* labels, in
 }
 
 dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, const dmrgc_options* opt,
-                             double* wall_seconds) {
+                             const float* rank_model, double* wall_seconds) {
   if (wall_seconds) *wall_seconds = 0.0;
   if (count < 0 || (count > 0 && !items) || n_workers < 1 || n_workers > 64) return DMRGC_EINVAL;
   for (int i = 0; i < count; ++i) {
@@ -1171,8 +1171,9 @@ dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, 
   }
   dmrgc_options base;
   if (opt) base = *opt; else dmrgc_default_options(&base);
-  // the learned mode needs a rank model per context: not offered here
-  if (base.precision < 0 || base.precision > 3 || base.svd_mode < 0 || base.svd_mode > 1) return DMRGC_EINVAL;
+  if (base.precision < 0 || base.precision > 3 || base.svd_mode < 0 || base.svd_mode > 2 ||
+      (base.svd_mode == 2 && !rank_model))
+    return DMRGC_EINVAL;
   if (count == 0) return DMRGC_OK;
   if (n_workers > count) n_workers = count;
   std::atomic<int> next{0};
@@ -1187,6 +1188,16 @@ dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, 
     dmrgc_ctx* c = new (std::nothrow) dmrgc_ctx();
     if (!c) { worker_status[wid] = DMRGC_ENOMEM; cudaStreamDestroy(st); return; }
     c->esz = 0;
+    c->st = st;
+    if (rank_model) {   // every worker's context gets its own copy of the model
+      const dmrgc_status ms = dmrgc_set_rank_model(c, rank_model);
+      if (ms != DMRGC_OK) {
+        worker_status[wid] = ms;
+        delete c;
+        cudaStreamDestroy(st);
+        return;
+      }
+    }
     for (;;) {
       const int i = next.fetch_add(1);
       if (i >= count) break;

@@ -69,3 +69,31 @@ def test_batch_reuse_across_sizes_and_mixed_precision():
     for r in res:
         assert r.status == 0
         assert abs(r.log_F_tilde) < 1e-4
+
+
+def test_batch_learned_mode_equals_single_context():
+    """svd_mode 2 in a batch: every worker loads the same rank model, so each
+    instance equals a single-context run with that model (FP64)."""
+    import numpy as np
+    from paper_2207_05612_gb300 import Context, binding
+    rng = np.random.default_rng(9)
+    model = (rng.normal(size=binding.MLP_PARAMS) * 0.05).astype(np.float32)
+    model[-1] = 3.0   # bias: predicts about 8 (2^3) kept values
+    cases = [(4, 4, 32, 6, 31), (3, 4, 16, 8, 32), (4, 5, 32, 6, 33)]
+    circs = [sc.random_circuit(r, c, cyc, seed=s) for (r, c, chi, cyc, s) in cases]
+    items, keep = binding.pack_batch([(r, c, chi, circ.layers, 2)
+                                      for (r, c, chi, _, _), circ in zip(cases, circs)])
+    opt = binding.dmrgc_default_options()
+    opt.svd_mode = 2
+    binding.dmrgc_batch_run(items, len(cases), 2, opt, rank_model=model)
+    for i, ((rows, cols, chi, cyc, seed), circ) in enumerate(zip(cases, circs)):
+        r = items[i]
+        assert r.status == 0
+        ctx = Context(rows, cols, chi, svd_mode=2)
+        ctx.set_rank_model(model)
+        for layer in circ.layers:
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+        lf, _ = ctx.fidelity()
+        ctx.close()
+        assert abs(r.log_F_tilde - lf) < 1e-12

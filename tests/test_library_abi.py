@@ -57,7 +57,7 @@ def test_batch_item_layout_and_host_validation():
     lib = binding.lib()
     wall = ctypes.c_double(-1.0)
     opt = binding.dmrgc_default_options()
-    assert lib.dmrgc_batch_run(None, 0, 1, ctypes.byref(opt), ctypes.byref(wall)) == 0
+    assert lib.dmrgc_batch_run(None, 0, 1, ctypes.byref(opt), None, ctypes.byref(wall)) == 0
     assert wall.value == 0.0
     circ = sc.random_circuit(2, 3, 2, seed=0)
     items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2), (2, 3, 4, circ.layers, 2)])
@@ -72,9 +72,12 @@ def test_batch_item_layout_and_host_validation():
     for name, mutate, workers in bad:
         items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2), (2, 3, 4, circ.layers, 2)])
         mutate(items[1])
-        st = lib.dmrgc_batch_run(items, 2, workers, ctypes.byref(opt), ctypes.byref(wall))
+        st = lib.dmrgc_batch_run(items, 2, workers, ctypes.byref(opt), None, ctypes.byref(wall))
         assert st == binding.DMRGC_EINVAL, name
         assert items[0].status == -1        # nothing ran, outputs untouched
     opt.precision = 7
     items, keep = binding.pack_batch([(2, 3, 4, circ.layers, 2)])
-    assert lib.dmrgc_batch_run(items, 1, 1, ctypes.byref(opt), ctypes.byref(wall)) == binding.DMRGC_EINVAL
+    assert lib.dmrgc_batch_run(items, 1, 1, ctypes.byref(opt), None, ctypes.byref(wall)) == binding.DMRGC_EINVAL
+    opt.precision = 0
+    opt.svd_mode = 2   # the learned mode without a rank model
+    assert lib.dmrgc_batch_run(items, 1, 1, ctypes.byref(opt), None, ctypes.byref(wall)) == binding.DMRGC_EINVAL
