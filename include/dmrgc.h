@@ -156,6 +156,16 @@ dmrgc_status dmrgc_fidelity(dmrgc_ctx* ctx, double* log_F_tilde, double* f_delta
 dmrgc_status dmrgc_amplitude(dmrgc_ctx* ctx, const unsigned char* bits, long long count,
                              double* out_re_im);
 
+/* <a|b>: inner product of the current states of two contexts (each the MPS
+ * after its last sweep, or its state before the first layer), out_re_im[2].
+ * With a a forward open run of the first layers from |0..0> and b a
+ * backward open run from |x> under the adjoints of the remaining layers
+ * (reversed, each gate U replaced by U^+), it is the closed-mode amplitude of
+ * Sec. IV.C with an empty middle section.  Both contexts must have the same
+ * grid and storage precision (else DMRGC_EINVAL); the contraction runs on a's
+ * stream and in a's arithmetic after b's stream is synchronised. */
+dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im);
+
 /* Draw count bitstrings from |<x|Psi>|^2 by sequential conditional sampling.
  * Bit i (MPS site order) of sample j is 0 iff u < p(0 | earlier bits), with
  * u the (j*N + i + 1)-th output of SplitMix64 seeded with `seed`, mapped to

@@ -99,13 +99,14 @@ def lib():
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), C.c_void_p, P(C.c_double)]
         L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
+        L.dmrgc_overlap.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         fp = C.c_void_p
         L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
         L.dmrgc_rank_records.argtypes = [C.c_void_p, fp, fp, C.c_int, P(C.c_int)]
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+        for name in ("dmrgc_overlap", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
                      "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
@@ -352,6 +353,13 @@ def dmrgc_mlp_predict(params: np.ndarray, x: np.ndarray, bf16: bool = True) -> n
     return out
 
 
+def dmrgc_overlap(ctx_a, ctx_b) -> complex:
+    """<a|b> of the two contexts' current states."""
+    out = np.zeros(2)
+    _check(lib().dmrgc_overlap(ctx_a, ctx_b, out.ctypes.data), ctx_a)
+    return complex(out[0], out[1])
+
+
 def dmrgc_set_jacobi_kernel(variant: int) -> None:
     """0: column-pair Jacobi kernel (default); 1: Gram-block kernel."""
     _check(lib().dmrgc_set_jacobi_kernel(int(variant)))
@@ -407,6 +415,10 @@ class Context:
 
     def rank_records(self):
         return dmrgc_rank_records(self.h)
+
+    def overlap(self, other: "Context") -> complex:
+        """<self|other> of the two current states."""
+        return dmrgc_overlap(self.h, other.h)
 
     def close(self):
         if self.h:

@@ -1332,6 +1332,49 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
   return sync(c);
 }
 
+dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
+  if (!a || !b || !out_re_im) return DMRGC_EINVAL;
+  dmrgc_ctx* c = a;   // errors are reported on a
+  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64)
+    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid and storage precision");
+  std::vector<int>* ba;
+  std::vector<int>* bb;
+  auto& sa = current_state(a, ba);
+  auto& sb = current_state(b, bb);
+  if (b->st != a->st) CK(cudaStreamSynchronize(b->st));   // b's tensors are read on a's stream
+  const size_t es = a->esz;
+  // E[alpha][beta] over the bonds of a and b, from the left: E <- A_i^+ (E B_i)
+  const void* e_in = a->one.p;
+  DevBuf* bufs[2] = {&a->envL, &a->envR};
+  for (int i = 0; i < a->N; ++i) {
+    const int la = (*ba)[i], ra = (*ba)[i + 1], lb = (*bb)[i], rb = (*bb)[i + 1];
+    TRY(ensure(a, a->T, (size_t)la * 2 * rb * es));
+    GemmArgs g;   // T[alpha][s][b'] = E[alpha][beta] B_i[beta][s][b']
+    g.M = la; g.N = 2 * rb; g.K = lb;
+    g.A = e_in; g.lda = lb; g.opA = OP_N;
+    g.B = sb[i].p; g.ldb = 2 * rb; g.opB = OP_N;
+    g.C = a->T.p; g.ldc = 2 * rb;
+    TRY(gemm(a, g));
+    DevBuf* out = bufs[i & 1];
+    TRY(ensure(a, *out, (size_t)ra * rb * es));
+    GemmArgs h;   // E'[a'][b'] = sum_{alpha, s} conj(A_i[alpha][s][a']) T[alpha][s][b']
+    h.M = ra; h.N = rb; h.K = 2 * la;
+    h.A = sa[i].p; h.lda = ra; h.opA = OP_C;
+    h.B = a->T.p; h.ldb = rb; h.opB = OP_N;
+    h.C = out->p; h.ldc = rb;
+    TRY(gemm(a, h));
+    e_in = out->p;
+  }
+  TRY(ensure(a, a->out_d, sizeof(double2)));
+  {
+    Span sp(a, TC_OTHER);
+    CK(to_complex128(e_in, 1, a->fp64, (double2*)a->out_d.p, a->st));
+    a->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(out_re_im, a->out_d.p, sizeof(double2), cudaMemcpyDeviceToHost, a->st));
+  return sync(a);
+}
+
 dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed, unsigned char* out_bits) {
   if (!c) return DMRGC_EINVAL;
   if (count < 0 || (count > 0 && !out_bits)) return fail(c, DMRGC_EINVAL, "bad sample arguments");

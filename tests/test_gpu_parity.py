@@ -294,3 +294,55 @@ def test_mpo_compression_keeps_the_layer(prec, tol):
     lf, _ = ctx.fidelity()
     assert abs(lf) < (1e-10 if prec == 0 else 1e-4)
     ctx.close()
+
+
+def _adjoint(layer):
+    """U^+ of a layer: its gates reversed, each conjugate-transposed."""
+    return [(q0, q1, np.asarray(u).conj().T) for (q0, q1, u) in reversed(layer)]
+
+
+def test_overlap_of_two_states_fp64():
+    """<a|b> of two exact 3x4 runs equals the statevector inner product, and
+    <a|a> = 1."""
+    from paper_2207_05612_gb300 import Context
+    ca, cb = sc.random_circuit(3, 4, 6, seed=41), sc.random_circuit(3, 4, 6, seed=42)
+    a, b = Context(3, 4, 64), Context(3, 4, 64)
+    for ctx, circ in ((a, ca), (b, cb)):
+        for layer in circ.layers:
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+    psi_a = sv.run(12, ca.layers)[-1]
+    psi_b = sv.run(12, cb.layers)[-1]
+    want = np.vdot(np.asarray(psi_a).ravel(), np.asarray(psi_b).ravel())
+    assert abs(a.overlap(b) - want) < 1e-10
+    assert abs(a.overlap(a) - 1.0) < 1e-10
+    a.close()
+    b.close()
+
+
+def test_closed_mode_amplitude_fp64():
+    """Closed mode (Sec. IV.C) with an empty middle: a forward run of the
+    first two layers from |0..0> and a backward run from |x> under the
+    adjoints of the last two give <x|U|0..0>; exact regime, so it equals the
+    statevector amplitude."""
+    from paper_2207_05612_gb300 import Context
+    circ = sc.random_circuit(3, 4, 8, seed=43)
+    assert len(circ.layers) == 4
+    fwd = Context(3, 4, 64)
+    for layer in circ.layers[:2]:
+        fwd.apply_layer(layer)
+        fwd.sweep(2)
+    exact = sv.run(12, circ.layers)[-1]
+    xgate = np.array([[0, 1], [1, 0]], dtype=complex)
+    for bits in sc.random_bitstrings(12, 4, seed=5):
+        bwd = Context(3, 4, 64)
+        bwd.apply_layer([(q, -1, xgate) for q in range(12) if bits[q]])
+        bwd.sweep(2)
+        for layer in reversed(circ.layers[2:]):
+            bwd.apply_layer(_adjoint(layer))
+            bwd.sweep(2)
+        amp = bwd.overlap(fwd)
+        want = sv.amplitudes(exact, bits[None, :])[0]
+        assert abs(amp - want) < 1e-10, (amp, want)
+        bwd.close()
+    fwd.close()
