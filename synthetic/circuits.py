@@ -16,6 +16,8 @@ Workload families (paper Sec. V.A "Three quantum circuits"):
   r+c even, C = horizontal with r+c odd, D = vertical with r+c odd.  Each
   qubit then meets at most one gate per cycle and the four patterns cover
   every grid edge once.
+* Sequence II: the same gates with the pattern order CDBA-BACD repeated
+  (Sec. V.A), which the paper found harder to simulate.
 * Sequence III, QAOA MaxCut (Sec. V.A): U = prod_k U_B(beta_k) U_C(gamma_k)
   with U_C = prod_{edges} exp(-i gamma Z_m Z_n) and U_B = prod_m exp(-i beta X_m),
   here on the nearest-neighbour grid graph, started from |+>^N (Hadamards on
@@ -90,6 +92,7 @@ def all_edges(rows: int, cols: int) -> list[tuple[int, int]]:
 
 
 PATTERN_ORDER = "ABCDCDAB"  # Sec. V.A: ABCD-CDAB-ABCD-...
+PATTERN_ORDER_II = "CDBABACD"  # Sequence II (Sec. V.A): CDBA-BACD-...
 
 
 @dataclass
@@ -106,8 +109,11 @@ class Circuit:
 
 def random_circuit(rows: int, cols: int, cycles: int, cycles_per_layer: int = 2,
                    seed: int = 0, theta: float = math.pi / 2,
-                   phi: float = math.pi / 6) -> Circuit:
-    """Sequence I on a rows x cols grid, grouped into layers of K cycles."""
+                   phi: float = math.pi / 6, pattern_order: str = PATTERN_ORDER) -> Circuit:
+    """Sequence I on a rows x cols grid, grouped into layers of K cycles
+    (pattern_order=PATTERN_ORDER_II gives Sequence II)."""
+    if not pattern_order or set(pattern_order) - set("ABCD"):
+        raise ValueError("pattern_order is a string over A, B, C, D")
     rng = np.random.default_rng(seed)
     n = rows * cols
     names = ("X", "Y", "W")
@@ -126,7 +132,7 @@ def random_circuit(rows: int, cols: int, cycles: int, cycles_per_layer: int = 2,
                 g = others[int(rng.integers(2))]
             prev[q] = g
             layer.append((q, -1, mats[names[g]].copy()))
-        for (a, b) in pats[PATTERN_ORDER[cyc % len(PATTERN_ORDER)]]:
+        for (a, b) in pats[pattern_order[cyc % len(pattern_order)]]:
             layer.append((a, b, two.copy()))
             circ.n_two_qubit += 1
         if (cyc + 1) % cycles_per_layer == 0 or cyc == cycles - 1:

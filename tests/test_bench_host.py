@@ -71,3 +71,20 @@ def test_batch_generator_mix():
     assert all(len(b.circuit.layers) == math.ceil(b.cycles / 2) for b in insts)
     again = sc.batch_instances(64, seed=0)
     assert [(b.rows, b.cycles, b.chi, b.seed) for b in insts] == [(b.rows, b.cycles, b.chi, b.seed) for b in again]
+
+
+def test_sequence_two_pattern_order():
+    """Sequence II uses the patterns in the order CDBA-BACD; every cycle is a
+    matching (no qubit twice) and eight cycles cover every grid edge twice."""
+    import collections
+    from synthetic import circuits as sc
+    c2 = sc.random_circuit(4, 5, 8, cycles_per_layer=1, seed=3, pattern_order=sc.PATTERN_ORDER_II)
+    pats = sc.grid_edges(4, 5)
+    count = collections.Counter()
+    for cyc, layer in enumerate(c2.layers):
+        pairs = [(a, b) for (a, b, u) in layer if b >= 0]
+        assert sorted(pairs) == sorted(pats[sc.PATTERN_ORDER_II[cyc]])
+        qs = [q for p in pairs for q in p]
+        assert len(qs) == len(set(qs))
+        count.update(tuple(sorted(p)) for p in pairs)
+    assert set(count.values()) == {2} and len(count) == len(sc.all_edges(4, 5))
