@@ -592,6 +592,7 @@ def batch_report(args):
     insts = sc.batch_instances(args.batch_count, seed=args.seed)
     opt = binding.dmrgc_default_options()
     opt.precision = prec
+    opt.mpo_compress = args.mpo_compress
 
     def run(subset, workers):
         items, keep = binding.pack_batch([(b.rows, b.cols, b.chi, b.circuit.layers, 2) for b in subset])
