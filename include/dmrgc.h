@@ -166,6 +166,15 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* ctx, const unsigned char* bits, long lon
  * stream and in a's arithmetic after b's stream is synchronised. */
 dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im);
 
+/* <a| U |b> for the gates of a middle section U (any number of cycles, in
+ * time order, as for dmrgc_apply_layer): the closed-mode amplitude of
+ * Sec. IV.C with the middle contracted exactly.  U becomes one exact MPO
+ * (its bond, the product of the straddling gates' Schmidt ranks, must stay
+ * <= 4096, else DMRGC_EINVAL) in a scratch context; a and b are not changed.
+ * Same requirements and stream as dmrgc_overlap. */
+dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* gates, int n_gates,
+                                 double* out_re_im);
+
 /* Draw count bitstrings from |<x|Psi>|^2 by sequential conditional sampling.
  * Bit i (MPS site order) of sample j is 0 iff u < p(0 | earlier bits), with
  * u the (j*N + i + 1)-th output of SplitMix64 seeded with `seed`, mapped to

@@ -100,13 +100,14 @@ def lib():
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), C.c_void_p, P(C.c_double)]
         L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
         L.dmrgc_overlap.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.dmrgc_overlap_layer.argtypes = [C.c_void_p, C.c_void_p, P(Gate), C.c_int, C.c_void_p]
         fp = C.c_void_p
         L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
         L.dmrgc_rank_records.argtypes = [C.c_void_p, fp, fp, C.c_int, P(C.c_int)]
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_overlap", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+        for name in ("dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
                      "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
@@ -360,6 +361,14 @@ def dmrgc_overlap(ctx_a, ctx_b) -> complex:
     return complex(out[0], out[1])
 
 
+def dmrgc_overlap_layer(ctx_a, ctx_b, gates) -> complex:
+    """<a| U |b> with U the given gates (one exact MPO)."""
+    packed = pack_gates(gates)
+    out = np.zeros(2)
+    _check(lib().dmrgc_overlap_layer(ctx_a, ctx_b, packed, len(gates), out.ctypes.data), ctx_a)
+    return complex(out[0], out[1])
+
+
 def dmrgc_set_jacobi_kernel(variant: int) -> None:
     """0: column-pair Jacobi kernel (default); 1: Gram-block kernel."""
     _check(lib().dmrgc_set_jacobi_kernel(int(variant)))
@@ -416,9 +425,12 @@ class Context:
     def rank_records(self):
         return dmrgc_rank_records(self.h)
 
-    def overlap(self, other: "Context") -> complex:
-        """<self|other> of the two current states."""
-        return dmrgc_overlap(self.h, other.h)
+    def overlap(self, other: "Context", gates=None) -> complex:
+        """<self|other> of the two current states, or <self| U |other> with
+        U the given gates."""
+        if gates is None:
+            return dmrgc_overlap(self.h, other.h)
+        return dmrgc_overlap_layer(self.h, other.h, gates)
 
     def close(self):
         if self.h:

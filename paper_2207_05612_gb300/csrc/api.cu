@@ -1375,6 +1375,71 @@ dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
   return sync(a);
 }
 
+dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* gates, int n_gates,
+                                 double* out_re_im) {
+  if (!a || !b || !out_re_im || n_gates < 0 || (n_gates > 0 && !gates)) return DMRGC_EINVAL;
+  dmrgc_ctx* c = a;   // errors are reported on a
+  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64)
+    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid and storage precision");
+  // the middle section's MPO lives in a scratch context on a's stream
+  dmrgc_options o = a->opt;
+  o.mpo_compress = 0;
+  o.svd_mode = 0;
+  o.log_rank_records = 0;
+  dmrgc_grid grid{a->rows, a->cols, 0};
+  dmrgc_ctx* m = nullptr;
+  dmrgc_status st = dmrgc_create(a->N, &grid, 1, &o, &m);
+  if (st != DMRGC_OK) return fail(a, st, "overlap: scratch context");
+  struct Guard { dmrgc_ctx* p; ~Guard() { dmrgc_destroy(p); } } guard{m};
+  st = build_mpo(m, gates, n_gates);
+  if (st != DMRGC_OK) return fail(a, st, std::string("overlap: ") + m->err);
+  if (b->st != a->st) CK(cudaStreamSynchronize(b->st));
+  CK(cudaStreamSynchronize(m->st));
+  std::vector<int>* ba;
+  std::vector<int>* bb;
+  auto& sa = current_state(a, ba);
+  auto& sb = current_state(b, bb);
+  const size_t es = a->esz;
+  // E[alpha][w][beta] from the left: X = E B_i W_i (as in the sweep), E <- A_i^+ X
+  const void* e_in = a->one.p;
+  DevBuf* bufs[2] = {&m->envL, &m->envR};
+  for (int i = 0; i < a->N; ++i) {
+    const int la = (*ba)[i], ra = (*ba)[i + 1], lb = (*bb)[i], rb = (*bb)[i + 1];
+    const int dw = m->D[i], dout = m->D[i + 1];
+    TRY(ensure(m, m->T, (size_t)la * dw * 2 * rb * es));
+    GemmArgs g1;   // T[alpha][w][t][b'] = E[alpha][w][beta] B_i[beta][t][b']
+    g1.M = la * dw; g1.N = 2 * rb; g1.K = lb;
+    g1.A = e_in; g1.lda = lb; g1.opA = OP_N;
+    g1.B = sb[i].p; g1.ldb = 2 * rb; g1.opB = OP_N;
+    g1.C = m->T.p; g1.ldc = 2 * rb;
+    TRY(gemm(a, g1));
+    TRY(ensure(m, m->jw, (size_t)la * 2 * dout * rb * es));
+    GemmArgs g2;   // X[alpha][s][w'][b'] = sum_{w,t} W[w][s][t][w'] T[alpha][w][t][b']
+    g2.M = 2 * dout; g2.N = rb; g2.K = 2 * dw; g2.b1 = la;
+    g2.A = m->Wx[i].p; g2.lda = 2 * dw; g2.sA1 = 0; g2.opA = OP_N;
+    g2.B = m->T.p; g2.ldb = rb; g2.sB1 = (long long)dw * 2 * rb; g2.opB = OP_N;
+    g2.C = m->jw.p; g2.ldc = rb; g2.sC1 = (long long)2 * dout * rb;
+    TRY(gemm(a, g2));
+    DevBuf* out = bufs[i & 1];
+    TRY(ensure(m, *out, (size_t)ra * dout * rb * es));
+    GemmArgs h;   // E'[a'][w'][b'] = sum_{alpha, s} conj(A_i[alpha][s][a']) X[alpha][s][w'][b']
+    h.M = ra; h.N = dout * rb; h.K = 2 * la;
+    h.A = sa[i].p; h.lda = ra; h.opA = OP_C;
+    h.B = m->jw.p; h.ldb = dout * rb; h.opB = OP_N;
+    h.C = out->p; h.ldc = dout * rb;
+    TRY(gemm(a, h));
+    e_in = out->p;
+  }
+  TRY(ensure(a, a->out_d, sizeof(double2)));
+  {
+    Span sp(a, TC_OTHER);
+    CK(to_complex128(e_in, 1, a->fp64, (double2*)a->out_d.p, a->st));
+    a->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(out_re_im, a->out_d.p, sizeof(double2), cudaMemcpyDeviceToHost, a->st));
+  return sync(a);
+}
+
 dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed, unsigned char* out_bits) {
   if (!c) return DMRGC_EINVAL;
   if (count < 0 || (count > 0 && !out_bits)) return fail(c, DMRGC_EINVAL, "bad sample arguments");

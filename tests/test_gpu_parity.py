@@ -346,3 +346,30 @@ def test_closed_mode_amplitude_fp64():
         assert abs(amp - want) < 1e-10, (amp, want)
         bwd.close()
     fwd.close()
+
+
+def test_closed_mode_exact_middle_fp64():
+    """Closed mode with an exact middle section: forward run of layer 1,
+    middle layer 2 contracted exactly as one MPO, backward run from |x>
+    under the adjoints of layers 4 and 3; equals the statevector amplitude.
+    An empty middle equals the plain overlap."""
+    from paper_2207_05612_gb300 import Context
+    circ = sc.random_circuit(3, 4, 8, seed=44)
+    fwd = Context(3, 4, 64)
+    fwd.apply_layer(circ.layers[0])
+    fwd.sweep(2)
+    exact = sv.run(12, circ.layers)[-1]
+    xgate = np.array([[0, 1], [1, 0]], dtype=complex)
+    for bits in sc.random_bitstrings(12, 3, seed=6):
+        bwd = Context(3, 4, 64)
+        bwd.apply_layer([(q, -1, xgate) for q in range(12) if bits[q]])
+        bwd.sweep(2)
+        for layer in reversed(circ.layers[2:]):
+            bwd.apply_layer(_adjoint(layer))
+            bwd.sweep(2)
+        amp = bwd.overlap(fwd, gates=circ.layers[1])
+        want = sv.amplitudes(exact, bits[None, :])[0]
+        assert abs(amp - want) < 1e-10, (amp, want)
+        assert abs(bwd.overlap(fwd, gates=[]) - bwd.overlap(fwd)) < 1e-12
+        bwd.close()
+    fwd.close()
