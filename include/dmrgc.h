@@ -182,6 +182,14 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
 dmrgc_status dmrgc_sample(dmrgc_ctx* ctx, long long count, unsigned long long seed,
                           unsigned char* out_bits);
 
+/* Linear cross-entropy benchmark (Eq. FB-sup, estimated as in Eq. FB-estim):
+ * draws `count` bit strings from `sampled` (dmrgc_sample with `seed`) and
+ * returns f_b = 2^N <p(x)> - 1 with p(x) = |<x|reference>|^2 from the
+ * reference context (for example an exact run at chi >= 2^(N/2)), and
+ * optionally the standard error of that mean.  count in 2 .. 2^26; N <= 62. */
+dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count, unsigned long long seed,
+                       double* f_b, double* stderr_out);
+
 /* Current bond dimensions of the MPS (n_qubits-1 entries) and of the layer
  * MPO (n_qubits-1 entries); either pointer may be NULL. */
 dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* ctx, int* mps_bonds, int* mpo_bonds);

@@ -100,6 +100,8 @@ def lib():
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), C.c_void_p, P(C.c_double)]
         L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
         L.dmrgc_overlap.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.dmrgc_xeb.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_ulonglong, P(C.c_double),
+                                P(C.c_double)]
         L.dmrgc_overlap_layer.argtypes = [C.c_void_p, C.c_void_p, P(Gate), C.c_int, C.c_void_p]
         fp = C.c_void_p
         L.dmrgc_set_rank_model.argtypes = [C.c_void_p, fp]
@@ -107,7 +109,7 @@ def lib():
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+        for name in ("dmrgc_xeb", "dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
                      "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
@@ -367,6 +369,13 @@ def dmrgc_overlap_layer(ctx_a, ctx_b, gates) -> complex:
     out = np.zeros(2)
     _check(lib().dmrgc_overlap_layer(ctx_a, ctx_b, packed, len(gates), out.ctypes.data), ctx_a)
     return complex(out[0], out[1])
+
+
+def dmrgc_xeb(ctx_sampled, ctx_reference, count: int, seed: int) -> tuple[float, float]:
+    """(F_B, standard error) of `count` samples of one context scored by the other."""
+    fb, se = C.c_double(), C.c_double()
+    _check(lib().dmrgc_xeb(ctx_sampled, ctx_reference, count, seed, C.byref(fb), C.byref(se)), ctx_sampled)
+    return fb.value, se.value
 
 
 def dmrgc_set_jacobi_kernel(variant: int) -> None:

@@ -1490,6 +1490,33 @@ dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed
   return sync(c);
 }
 
+dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count, unsigned long long seed,
+                       double* f_b, double* stderr_out) {
+  if (!sampled || !reference || !f_b || count < 2 || count > (1LL << 26)) return DMRGC_EINVAL;
+  dmrgc_ctx* c = sampled;
+  if (sampled->N != reference->N || sampled->rows != reference->rows || sampled->cols != reference->cols)
+    return fail(c, DMRGC_EINVAL, "xeb needs two contexts on the same grid");
+  if (sampled->N > 62) return fail(c, DMRGC_EINVAL, "xeb: 2^N does not fit");
+  const int N = sampled->N;
+  std::vector<unsigned char> bits((size_t)count * N);
+  TRY(dmrgc_sample(sampled, count, seed, bits.data()));
+  std::vector<double> amp((size_t)count * 2);
+  const dmrgc_status st = dmrgc_amplitude(reference, bits.data(), count, amp.data());
+  if (st != DMRGC_OK) return fail(c, st, std::string("xeb: ") + reference->err);
+  // F_B = 2^N <p(x)> - 1 over the samples x (Eq. FB-estim); p = |<x|reference>|^2
+  const double scale = std::ldexp(1.0, N);
+  double sum = 0, sum2 = 0;
+  for (long long j = 0; j < count; ++j) {
+    const double p = amp[2 * j] * amp[2 * j] + amp[2 * j + 1] * amp[2 * j + 1];
+    sum += scale * p;
+    sum2 += scale * p * scale * p;
+  }
+  const double mean = sum / count;
+  *f_b = mean - 1.0;
+  if (stderr_out) *stderr_out = std::sqrt(std::max(sum2 / count - mean * mean, 0.0) / (count - 1));
+  return DMRGC_OK;
+}
+
 dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* c, int* mps_bonds, int* mpo_bonds) {
   if (!c) return DMRGC_EINVAL;
   const std::vector<int>& b = c->phase == 1 ? c->chiA : c->chiB;

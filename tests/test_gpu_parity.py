@@ -373,3 +373,25 @@ def test_closed_mode_exact_middle_fp64():
         assert abs(bwd.overlap(fwd, gates=[]) - bwd.overlap(fwd)) < 1e-12
         bwd.close()
     fwd.close()
+
+
+def test_xeb_estimator_fp64():
+    """Linear XEB from the MPS sampler scored by an exact run: for the exact
+    state its mean is 2^N sum_x p(x)^2 - 1 (statevector), within 5 standard
+    errors; a truncated run scores lower."""
+    from paper_2207_05612_gb300 import Context, binding
+    circ = sc.random_circuit(3, 4, 8, seed=45)
+    exact = Context(3, 4, 64)
+    trunc = Context(3, 4, 4)
+    for layer in circ.layers:
+        for ctx in (exact, trunc):
+            ctx.apply_layer(layer)
+            ctx.sweep(2)
+    psi = np.asarray(sv.run(12, circ.layers)[-1]).ravel()
+    want = 2 ** 12 * np.sum(np.abs(psi) ** 4) - 1.0
+    fb, se = binding.dmrgc_xeb(exact.h, exact.h, 20000, 3)
+    assert abs(fb - want) < 5 * se, (fb, want, se)
+    fb_t, se_t = binding.dmrgc_xeb(trunc.h, exact.h, 20000, 4)
+    assert fb_t < fb
+    exact.close()
+    trunc.close()
