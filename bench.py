@@ -55,6 +55,13 @@ N_SMS = 152
 
 # ------------------------------------------------------------------ helpers
 
+T_START = time.perf_counter()
+
+
+def note(msg: str) -> None:
+    """Progress line on stderr (the JSON result is the only stdout line)."""
+    print(f"[bench {time.perf_counter() - T_START:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
 
 def measured_peaks():
     try:
@@ -145,31 +152,47 @@ def alu_peak_tflops(fp64: bool, sm_mhz: float | None) -> float:
 # --------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(chi: int = 512, d_mpo: int = 64, seed: int = 0):
-    """One oracle two-site update at a bulk bond of the 54-qubit workload:
-    chi on both outer bonds, MPO bond D on the three cuts (a CD-layer bulk
-    bond), random isometric MPS tensors and random MPO tensors (the cost does
-    not depend on the values).  Returns (seconds, threads)."""
+def workload_shapes(rows: int, cols: int, chi: int, layer, compress: bool = True):
+    """Per bond (i, i+1) of a saturated step of the workload, the operand
+    shapes of one two-site update: MPS bonds min(2^i, 2^(N-i), chi) (old and
+    new state alike) and the layer MPO's bonds (the oracle's MPO of the given
+    layer, compressed like the bench's).  Returns [(chi_l, D_l, chi_m, D_m,
+    chi_r, D_r)] for bonds 0..N-2."""
+    from oracle import mpo as om
+    n = rows * cols
+    order = om.snake_order(rows, cols)
+    dmpo = [1] + om.bond_dims(om.layer_mpo(layer, order, compress=compress)) + [1]
+    chib = [min(2 ** min(i, n - i), chi) for i in range(n + 1)]
+    return [(chib[i], dmpo[i], chib[i + 1], dmpo[i + 1], chib[i + 2], dmpo[i + 2]) for i in range(n - 1)]
+
+
+def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 << 30):
+    """Oracle two-site updates (Sec. IV.B: X, Y, theta, truncated SVD, left
+    environment) on random tensors of the given shapes, bonds drawn uniformly
+    from `shapes` (the cost does not depend on the values), until budget_s of
+    CPU time or max_updates.  Returns (updates, seconds, threads, bonds)."""
     from oracle import dmrg as od
     rng = np.random.default_rng(seed)
 
     def rnd(*shape):
         return rng.normal(size=shape) + 1j * rng.normal(size=shape)
 
-    lenv = rnd(chi, d_mpo, chi)
-    renv = rnd(chi, d_mpo, chi)
-    b1 = rnd(chi, 2, chi)
-    b2 = rnd(chi, 2, chi)
-    w1 = rnd(d_mpo, 2, 2, d_mpo)
-    w2 = rnd(d_mpo, 2, 2, d_mpo)
-    t0 = time.perf_counter()
-    x = od.make_x(lenv, b1, w1)
-    y = od.make_y(renv, b2, w2)
-    th = od.theta_of(x, y)
-    u, s, vh, _ = od.svd_truncate(th, chi, 1e-12)
-    a1 = u.reshape(chi, 2, -1)
-    od.env_left(a1, x)
-    dt = time.perf_counter() - t0
+    done, spent, picked = 0, 0.0, []
+    while done < max_updates and (done == 0 or spent < budget_s):
+        i = int(rng.integers(len(shapes)))
+        cl, dl, cm, dm, cr, dr = shapes[i]
+        lenv, renv = rnd(cl, dl, cl), rnd(cr, dr, cr)
+        b1, b2 = rnd(cl, 2, cm), rnd(cm, 2, cr)
+        w1, w2 = rnd(dl, 2, 2, dm), rnd(dm, 2, 2, dr)
+        t0 = time.perf_counter()
+        x = od.make_x(lenv, b1, w1)
+        y = od.make_y(renv, b2, w2)
+        th = od.theta_of(x, y)
+        u, s, vh, _ = od.svd_truncate(th, cm, 1e-12)
+        od.env_left(u.reshape(cl, 2, -1), x)
+        spent += time.perf_counter() - t0
+        done += 1
+        picked.append(i)
     threads = os.cpu_count() or 1
     try:
         from threadpoolctl import threadpool_info
@@ -178,10 +201,18 @@ def oracle_sample(chi: int = 512, d_mpo: int = 64, seed: int = 0):
             threads = max(int(i.get("num_threads", 1)) for i in info)
     except Exception:
         pass
-    return dt, threads
+    return done, spent, threads, picked
 
 
 # ------------------------------------------------------------------- main
+
+
+STAT_KEYS = ("gemm_ms", "gemm_flops", "svd_ms", "svd_flops", "mpo_ms", "other_ms", "kernel_launches",
+             "jacobi_sweeps", "svd_launches", "updates", "eig_svds", "eig_fallbacks")
+
+
+def stats_delta(a: dict, b: dict) -> dict:
+    return {k: b[k] - a[k] for k in STAT_KEYS}
 
 
 def run_ours(args, world, rank, local):
@@ -208,15 +239,27 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     prec = PRECISIONS[args.precision]
     ctx = Context(rows, cols, args.chi, precision=prec, timing=True, stream=stream.cuda_stream,
-                  mpo_compress=args.mpo_compress)
+                  mpo_compress=args.mpo_compress, svd_path=args.svd_path)
     packed = [binding.pack_gates(l) for l in circ.layers[:args.warmup]]
     bits = sc.random_bitstrings(n, 1024, seed=7)
     upd_per_step = 2 * (n - 1)
+    lf_20 = None
 
     # warm-up steps: grow the bonds to chi
     for li in range(args.warmup):
         binding._check(binding.lib().dmrgc_apply_layer(ctx.h, packed[li], len(circ.layers[li])), ctx.h)
         ctx.sweep(2)
+        if li == 9:
+            lf_20 = ctx.fidelity()[0]
+        st_w = ctx.stats()
+        note(f"warm-up layer {li}: max bond {max(ctx.bond_dims()[0])}, svd {st_w['svd_ms']:.0f} ms, "
+             f"gemm {st_w['gemm_ms']:.0f} ms, eigensolver {st_w['eig_svds']} / fallbacks {st_w['eig_fallbacks']}")
+    # the warmed state, for the FP64 comparison on the first timed layer
+    warm = None
+    if args.fp64_updates > 0 and world == 1 and args.precision != "fp64":
+        mps, _ = ctx.get_mps()
+        lf_w, fd_w = ctx.fidelity()
+        warm = (mps, lf_w)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -226,6 +269,9 @@ def run_ours(args, world, rank, local):
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     h2d = d2h = 0
+    dev_stats = None
+    readout = None
+    hist0 = None
     t_region0 = time.perf_counter()
     for k in range(args.steps):
         li = args.warmup + k
@@ -239,10 +285,19 @@ def run_ours(args, world, rank, local):
         binding._check(binding.lib().dmrgc_apply_layer(ctx.h, gates, len(layer)), ctx.h)
         ctx.sweep(2)
         ev[2 * k + 1].record(stream)
-        ctx.fidelity()
+        s_dev = ctx.stats()            # the sweep synchronised: its kernels are counted
+        if k == 0:
+            hist0 = ctx.history()
+        lf_k, _ = ctx.fidelity()
+        if li == 9:
+            lf_20 = lf_k
         amps = ctx.amplitude(bits)
+        s_out = ctx.stats()
+        d = stats_delta(s_dev, s_out)
+        readout = d if readout is None else {key: readout[key] + d[key] for key in STAT_KEYS}
         h2d += len(layer) * 264 + bits.nbytes
         d2h += amps.size * 16 + 16
+        note(f"timed step {k}: svd {s_dev['svd_ms']:.0f} ms, gemm {s_dev['gemm_ms']:.0f} ms (cumulative)")
     torch.cuda.synchronize()
     t_region = time.perf_counter() - t_region0
     if world > 1:
@@ -250,18 +305,60 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     clk = clocks.stop()
     dev_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
-    st = ctx.stats()
+    st_all = ctx.stats()
+    st = {key: st_all[key] - readout[key] for key in STAT_KEYS}   # the device-timed part only
     dev_s = aggregate(dev_ms / 1e3, world, reduce_max)
     region_s = aggregate(t_region, world, reduce_max)
     total_updates = upd_per_step * args.steps * world
     lf, fd = ctx.fidelity()
     bonds, dmpo = ctx.bond_dims()
-    return {
+    out = {
         "ctx": ctx, "dev_s": dev_s, "region_s": region_s, "updates": total_updates, "stats": st,
-        "clocks": clk, "h2d": h2d // args.steps, "d2h": d2h // args.steps, "log_ft": lf,
-        "f_delta": fd, "max_chi": max(bonds), "max_D": max(dmpo), "rank": rank,
+        "readout": readout, "clocks": clk, "h2d": h2d // args.steps, "d2h": d2h // args.steps, "log_ft": lf,
+        "log_ft_20_cycles": lf_20, "f_delta": fd, "max_chi": max(bonds), "max_D": max(dmpo), "rank": rank,
         "n2g": sum(1 for l in circ.layers[:args.warmup + args.steps] for g in l if g[1] >= 0),
+        "first_layer": circ.layers[args.warmup], "vs_fp64": None,
     }
+    if warm is not None:
+        note("FP64 comparison")
+        out["vs_fp64"] = fp64_comparison(args, warm, circ.layers[args.warmup], hist0, stream, upd_per_step)
+        note(f"FP64 comparison done: {out['vs_fp64']}")
+    return out
+
+
+def fp64_comparison(args, warm, layer, hist_mixed, stream, upd_per_step):
+    """The plain FP64 GPU path on the first timed layer from the same warmed
+    state (loaded with set_mps): apply_layer (MPO build and zip-up guess) and
+    the first --fp64-updates updates of its sweep, each timed with CUDA events;
+    the partial fidelities of those updates against the mixed run's."""
+    import torch
+    from paper_2207_05612_gb300 import Context
+    mps, lf_w = warm
+    ctx = Context(args.rows, args.cols, args.chi, precision=PRECISIONS["fp64"], timing=True,
+                  stream=stream.cuda_stream, mpo_compress=args.mpo_compress)
+    ctx.set_mps(mps, lf_w)
+    note("FP64: state loaded")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    ctx.apply_layer(layer)
+    e[1].record(stream)
+    ctx.sweep_updates(args.fp64_updates)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e[0].elapsed_time(e[1])
+    upd_ms = e[1].elapsed_time(e[2])
+    h64 = np.array(ctx.history())
+    hm = np.array(hist_mixed[:len(h64)])
+    ctx.close()
+    per_update = upd_ms / 1e3 / max(1, args.fp64_updates)
+    step_s = apply_ms / 1e3 + per_update * upd_per_step
+    return {"updates_per_s": 1.0 / per_update,
+            "step_updates_per_s_estimate": upd_per_step / step_s,
+            "apply_layer_s": apply_ms / 1e3, "updates_timed": int(args.fp64_updates), "updates_s": upd_ms / 1e3,
+            "max_rel_diff_partial_fidelity": float(np.max(np.abs(h64 - hm) / hm)) if len(hm) else None,
+            "sample": f"FP64 context loaded with the warmed state (set_mps), the first timed layer: apply_layer "
+                      f"and the first {args.fp64_updates} updates of its sweep, CUDA events; "
+                      "step estimate = apply_layer + 106 x the mean update time"}
 
 
 def main(argv=None):
@@ -278,6 +375,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
                     help="complex64 Jacobi kernel for m <= 1024")
+    ap.add_argument("--svd-path", type=int, default=0, choices=[0, 1],
+                    help="0 (default): Gram eigensolver where it resolves the kept spectrum, else Jacobi; "
+                         "1: Jacobi only")
+    ap.add_argument("--fp64-updates", type=int, default=6,
+                    help="updates of the FP64 comparison on the first timed layer (0: skip)")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle CPU time for cpu_baseline")
     ap.add_argument("--mpo-compress", type=int, default=1, choices=[0, 1],
                     help="1 (default): lossless compression of each layer MPO before the guess; "
                          "0: the bond is the product of the straddling gates' Schmidt ranks")
@@ -311,22 +414,29 @@ def main(argv=None):
     config = {"workload": workload, "grid": f"{args.rows}x{args.cols}", "chi": args.chi,
               "cycles_per_step": 2, "sweeps_per_step": 2,
               "updates_per_step": 2 * (args.rows * args.cols - 1),
-              "jacobi_kernel": args.jacobi,
+              "jacobi_kernel": args.jacobi, "svd_path": "gram eigensolver + jacobi fallback" if args.svd_path == 0
+              else "jacobi",
               "mpo": "compressed (operator Schmidt ranks)" if args.mpo_compress else "product of gate Schmidt ranks",
               "l2": "inputs larger than L2 (environment caches of GBs), no flush"}
 
     if args.impl == "reference":
         if rank != 0:
             return 0
+        from synthetic import circuits as sc
+        circ = sc.random_circuit(args.rows, args.cols, max(20, 2 * (args.warmup + args.steps)), seed=args.seed)
+        shapes = workload_shapes(args.rows, args.cols, args.chi, circ.layers[args.warmup],
+                                 compress=bool(args.mpo_compress))
         times = []
         threads = 1
         for k in range(args.warmup + args.steps):
-            dt, threads = oracle_sample(args.chi, 64, seed=k)
+            done, dt, threads, _ = oracle_updates(shapes, 0.0, seed=k, max_updates=1)
             if k >= args.warmup:
                 times.append(dt)
         tot = sum(times)
         value = args.steps / tot
-        sample = f"one oracle two-site update at a bulk bond (chi={args.chi} both sides, MPO bond 64), per step"
+        sample = (f"per step one oracle two-site update at a bond drawn uniformly from the first timed layer's "
+                  f"bonds (the workload's operand shapes: saturated MPS bonds <= {args.chi}, the layer's "
+                  f"compressed MPO bonds; random values)")
         line = {"impl": "reference", "metric": "two-site updates/s", "value": value,
                 "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -365,26 +475,30 @@ def main(argv=None):
                      "peak": gpeak, "unit": "TFLOP/s", "frac": gemm_ach / gpeak, "traffic": None,
                      "peak_note": "CUDA-core FMA peak at the sampled SM clock"}
     spk = alu_peak_tflops(fp64, clk.get("sm_mhz"))
-    roof_svd = {"bound": "alu", "kernel": "jacobi kernels (one-sided Jacobi SVD)", "achieved": svd_ach,
-                "peak": spk, "unit": "TFLOP/s", "frac": svd_ach / spk, "traffic": None,
+    roof_svd = {"bound": "alu", "kernel": "truncated SVD (Gram eigensolver: he_tridiag, tri_*, he_backtrans; "
+                                          "Jacobi where it falls back)",
+                "achieved": svd_ach, "peak": spk, "unit": "TFLOP/s", "frac": svd_ach / spk, "traffic": None,
                 "peak_note": "CUDA-core FMA peak: 152 SMs x 128 FP32 lanes x 2 x sampled SM clock"
-                             if not fp64 else "nominal FP64 1.25 TFLOP/s x sampled/max SM clock"}
+                             if not fp64 else "nominal FP64 1.25 TFLOP/s x sampled/max SM clock",
+                "work_note": "algorithmic flops: 16/3 n^3 + 8 n^2 k per Gram eigensolver SVD, "
+                             "Jacobi 16 m per pair visited + 14 m per rotation"}
     if args.precision == "bf16x3":
         t = NCU_TRAFFIC["tc_gemm_bf16x3"]
         roof_gemm["traffic"] = t["bytes"]
         roof_gemm["traffic_note"] = f"ncu, one launch of {t['launch']} ({t['profile']})"
-    if not fp64 and args.jacobi == "wp4":
-        t = NCU_TRAFFIC["jacobi_wp4"]
-        roof_svd["traffic"] = t["bytes"]
-        roof_svd["traffic_note"] = (f"ncu, one launch of {t['launch']} ({t['profile']}); "
-                                    "achieved is the class aggregate over all launch sizes")
     roof = roof_gemm if st["gemm_ms"] >= st["svd_ms"] else roof_svd
     roof_other = roof_svd if roof is roof_gemm else roof_gemm
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dt, threads = oracle_sample(args.chi, 64)
-        cpu = {"value": 1.0 / dt, "unit": "updates/s", "cores": threads, "kind": "oracle",
-               "sample": f"one oracle two-site update at a bulk bond (chi={args.chi} both sides, MPO bond 64), {dt:.1f} s"}
+        note("CPU baseline")
+        shapes = workload_shapes(args.rows, args.cols, args.chi, r["first_layer"], compress=bool(args.mpo_compress))
+        done, spent, threads, picked = oracle_updates(shapes, args.cpu_budget, seed=1)
+        note(f"CPU baseline: {done} updates in {spent:.1f} s")
+        cpu = {"value": done / spent, "unit": "updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"{done} oracle two-site updates at bonds drawn uniformly from the timed layer's "
+                         f"{len(shapes)} bonds (operand shapes of the workload: saturated MPS bonds <= {args.chi}, "
+                         f"the layer's compressed MPO bonds; random values), {spent:.1f} s of CPU time, "
+                         f"bonds {sorted(picked)}"}
     line = {
         "metric": "two-site updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps,
@@ -395,18 +509,23 @@ def main(argv=None):
         "roofline": roof,
         "roofline_secondary": roof_other,
         "cpu_baseline": cpu,
+        "vs_fp64": r["vs_fp64"],
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                    "reasons": clk.get("reasons")},
-        "gpu_launches": int(st["kernel_launches"]),
+        "gpu_launches": int(st["kernel_launches"] + r["readout"]["kernel_launches"]),
         "fidelity": {"log_F_tilde": r["log_ft"], "f_delta_last": r["f_delta"],
                      "eps_tilde": float(1 - np.exp(r["log_ft"] / max(1, r["n2g"]))),
-                     "n_2q_gates": r["n2g"]},
+                     "n_2q_gates": r["n2g"], "cycles": 2 * (args.warmup + args.steps),
+                     "log_F_tilde_after_20_cycles": r["log_ft_20_cycles"]},
         "breakdown_ms": {"gemm": st["gemm_ms"], "svd": st["svd_ms"], "mpo": st["mpo_ms"],
                          "other": st["other_ms"],
                          "gemm_tflops": st["gemm_flops"] / max(gemm_s, 1e-12) / 1e12,
                          "svd_tflops": st["svd_flops"] / max(svd_s, 1e-12) / 1e12,
-                         "jacobi_sweeps_per_svd": st["jacobi_sweeps"] / max(1, st["svd_launches"] / 4),
-                         "jacobi_sweeps_per_update": st["jacobi_sweeps"] / max(1, st["updates"])},
+                         "eig_svds": st["eig_svds"], "eig_fallbacks": st["eig_fallbacks"],
+                         "jacobi_sweeps": st["jacobi_sweeps"],
+                         "note": "device-timed part only (apply_layer + sweeps)"},
+        "readout_ms": {"amplitudes_1024": r["readout"]["gemm_ms"] + r["readout"]["other_ms"],
+                       "note": "per run, outside value, inside e2e"},
         "state": {"max_chi": r["max_chi"], "max_D": r["max_D"]},
     }
     print(json.dumps(line))

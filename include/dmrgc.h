@@ -92,6 +92,15 @@ typedef struct {
                                  (Jacobi SVD of the site tensors, two passes, cut at the
                                  sweep cutoff); 0 (default): the bond is the product of the
                                  straddling gates' Schmidt ranks */
+  int svd_path;               /* complex64 modes, truncated SVDs of 128..2048 rows that keep
+                                 fewer than all of them (the sweep's theta, the zip-up's Gram):
+                                 0 (default) = the leading eigenvectors of the Gram matrix
+                                 G G^+ (TF32x3 product, Householder tridiagonalisation,
+                                 bisection and FP64 inverse iteration, back-transformation)
+                                 whenever every kept eigenvalue is at least 1e-4 of the largest
+                                 (the Gram's rounding then cannot move the kept subspace), the
+                                 Jacobi SVD otherwise; 1 = always the Jacobi SVD.  FP64 mode
+                                 always uses the Jacobi SVD. */
 } dmrgc_options;
 
 typedef struct {
@@ -105,10 +114,12 @@ typedef struct {
 typedef struct {
   double gemm_ms, gemm_flops;   /* all contractions (environments, X/Y, theta, Gram, gauge) */
   long long gemm_launches;
-  double svd_ms;                /* Jacobi SVD incl. sort/gather */
-  double svd_flops;             /* algorithmic real flops of the Jacobi kernels: 16 per complex
-                                   element for the three dot products of every pair visited,
-                                   14 per element for every rotation applied */
+  double svd_ms;                /* truncated SVDs (Jacobi incl. sort/gather; Gram eigensolver
+                                   without its Gram product, which counts as a contraction) */
+  double svd_flops;             /* algorithmic real flops: Jacobi kernels 16 per complex element
+                                   for the three dot products of every pair visited, 14 per
+                                   element for every rotation applied; Gram eigensolver
+                                   16/3 n^3 (tridiagonalisation) + 8 n^2 k (back-transformation) */
   long long svd_launches;
   long long jacobi_sweeps;      /* Jacobi sweeps executed (sum over SVDs) */
   double mpo_ms;                /* layer MPO build */
@@ -117,6 +128,8 @@ typedef struct {
   long long kernel_launches;    /* every kernel the library launched */
   long long rsvd_attempts;      /* randomized SVDs tried (svd_mode 1, 2) */
   long long rsvd_accepted;      /* of which accepted (the rest fell back to Jacobi) */
+  long long eig_svds;           /* truncated SVDs done by the Gram eigensolver (svd_path 0) */
+  long long eig_fallbacks;      /* Gram eigensolver results not resolved: redone by Jacobi */
 } dmrgc_stats;
 
 /* Fill *opt with defaults (FP64, Jacobi, default cutoffs, default stream). */
@@ -200,6 +213,21 @@ dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* ctx, int* mps_bonds, int* mpo_bond
 long long dmrgc_mps_size(const dmrgc_ctx* ctx);
 dmrgc_status dmrgc_get_mps(const dmrgc_ctx* ctx, double* out_re_im, int* centre);
 
+/* Load an MPS (checkpoint restore): site i has shape [bonds[i]][2][bonds[i+1]]
+ * (row-major complex128, concatenated, the layout of dmrgc_get_mps), bonds[0]
+ * = bonds[N] = 1 and 1 <= bonds[i] <= chi.  The tensors are converted to the
+ * context's storage precision and become the state the next
+ * dmrgc_apply_layer compresses (|Psi_Q> of Sec. IV.B); log_F_tilde is the
+ * running Eq. (Ftilde-sup) sum to continue from.  A state saved with
+ * dmrgc_get_mps after a step (centre on site N/2, the canonical form the sweep
+ * leaves) and loaded here continues the run as if it had not stopped, up to
+ * the rounding of a change of storage precision. */
+dmrgc_status dmrgc_set_mps(dmrgc_ctx* ctx, const double* in_re_im, const int* bonds, double log_F_tilde);
+
+/* The next n_updates two-site updates of the current step on the schedule
+ * of dmrgc_sweep (which runs n_sweeps * (N-1) of them); f_last as there. */
+dmrgc_status dmrgc_sweep_updates(dmrgc_ctx* ctx, long long n_updates, double* f_last);
+
 /* Per-update partial fidelities of the current step (Sec. IV.B.1: they never
  * decrease).  Writes min(cap, count) values; *count receives the number done. */
 dmrgc_status dmrgc_step_history(const dmrgc_ctx* ctx, double* f, int cap, int* count);
@@ -230,12 +258,32 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out);
 
+/* dmrgc_test_svd_gram: the sweep's other truncated SVD (options.svd_path 0):
+ * the leading eigenvectors of H = G G^+ (m x m, TF32x3 product; FP32 for
+ * precision DMRGC_FP32) by Householder tridiagonalisation, bisection, FP64
+ * inverse iteration and back-transformation (the kept left singular vectors
+ * of G, Eq. optimization with the bond constraint).  Complex64 precisions
+ * only (1..3); 3 <= m <= 2048; 1 <= chi < m.  s_out[m]: the min(chi+1, m)
+ * leading singular values, zeros after; U_out[m][k] row-major.  *k_out = k,
+ * or -1 when the kept eigenvalues are not all resolved (lambda_{k-1} < 1e-4
+ * lambda_0, or the cut rel_cut set k): the sweep then uses the Jacobi SVD. */
+dmrgc_status dmrgc_test_svd_gram(int precision, int m, int n, const double* G, int chi, double rel_cut,
+                                 double* s_out, int* k_out, double* U_out);
+
 /* Tuning: the Jacobi kernel for complex64 matrices of at most 1024 rows
  * (process-wide).  0 (default): column pairs, one warp per column, two
  * 4-column blocks per CTA; 1: 8 x 8 Gram blocks, rows spread over 512 threads,
  * one Jacobi sweep of the Gram per round.  Both compute the same
  * decomposition to working precision.  Other values: DMRGC_EINVAL. */
 dmrgc_status dmrgc_set_jacobi_kernel(int variant);
+
+/* Failure handling: the iteration limit of every spin wait of the Jacobi
+ * kernels on the current device (the bounded grid barrier and the per-block
+ * round counters; one poll is about 64 ns).  A wait that runs out sets the
+ * launch's error flag, every CTA leaves at its next wait, and the calling
+ * entry point returns DMRGC_ETIMEOUT; the context stays usable.  0 restores
+ * the default (2e7 polls, about 1.3 s).  Process-wide per device. */
+dmrgc_status dmrgc_set_wait_limit(unsigned long long spins);
 
 /* ---- Rank model (svd_mode 2)
  *

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("timing", C.c_int),
                 ("rsvd_oversample", C.c_int), ("rsvd_power_iters", C.c_int),
                 ("rsvd_tolerance", C.c_double), ("log_rank_records", C.c_int),
-                ("mpo_compress", C.c_int)]
+                ("mpo_compress", C.c_int), ("svd_path", C.c_int)]
 
 
 class Gate(C.Structure):
@@ -49,7 +49,8 @@ class Stats(C.Structure):
                 ("svd_ms", C.c_double), ("svd_flops", C.c_double), ("svd_launches", C.c_longlong),
                 ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
                 ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong),
-                ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong)]
+                ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong),
+                ("eig_svds", C.c_longlong), ("eig_fallbacks", C.c_longlong)]
 
 
 class BatchItem(C.Structure):
@@ -95,10 +96,15 @@ def lib():
                                       C.c_longlong, C.c_longlong, C.c_void_p]
         L.dmrgc_test_svd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                      C.c_void_p, P(C.c_int), C.c_void_p]
+        L.dmrgc_test_svd_gram.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                                          C.c_void_p, P(C.c_int), C.c_void_p]
         L.dmrgc_svd_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                         C.c_void_p, P(C.c_int), C.c_void_p, C.c_void_p]
         L.dmrgc_batch_run.argtypes = [P(BatchItem), C.c_int, C.c_int, P(Options), C.c_void_p, P(C.c_double)]
         L.dmrgc_set_jacobi_kernel.argtypes = [C.c_int]
+        L.dmrgc_set_wait_limit.argtypes = [C.c_ulonglong]
+        L.dmrgc_set_mps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]
+        L.dmrgc_sweep_updates.argtypes = [C.c_void_p, C.c_longlong, P(C.c_double)]
         L.dmrgc_overlap.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.dmrgc_xeb.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_ulonglong, P(C.c_double),
                                 P(C.c_double)]
@@ -109,8 +115,8 @@ def lib():
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_xeb", "dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
-                     "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
+        for name in ("dmrgc_set_mps", "dmrgc_sweep_updates", "dmrgc_set_wait_limit", "dmrgc_xeb", "dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+                     "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_test_svd_gram", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
             getattr(L, name).restype = C.c_int
@@ -205,6 +211,20 @@ def dmrgc_get_mps(ctx, n_qubits: int) -> tuple[list[np.ndarray], int]:
     return out, centre.value
 
 
+def dmrgc_set_mps(ctx, mps, log_ft: float = 0.0) -> None:
+    """Load an MPS (list of [chi_l, 2, chi_r] arrays, the layout of
+    dmrgc_get_mps) as the state the next apply_layer compresses."""
+    bonds = np.array([mps[0].shape[0]] + [a.shape[2] for a in mps], dtype=np.int32)
+    flat = np.concatenate([np.ascontiguousarray(a, dtype=np.complex128).reshape(-1) for a in mps])
+    _check(lib().dmrgc_set_mps(ctx, flat.ctypes.data, bonds.ctypes.data, float(log_ft)), ctx)
+
+
+def dmrgc_sweep_updates(ctx, n_updates: int) -> float:
+    f = C.c_double()
+    _check(lib().dmrgc_sweep_updates(ctx, int(n_updates), C.byref(f)), ctx)
+    return f.value
+
+
 def dmrgc_step_history(ctx) -> list[float]:
     n = C.c_int()
     _check(lib().dmrgc_step_history(ctx, None, 0, C.byref(n)), ctx)
@@ -250,6 +270,23 @@ def dmrgc_test_svd(precision: int, g: np.ndarray, chi: int, rel_cut: float):
     _check(lib().dmrgc_test_svd(precision, m, n, gc.ctypes.data, chi, rel_cut, s.ctypes.data,
                                 C.byref(k), u.ctypes.data))
     kk = k.value
+    return s, kk, u.reshape(-1)[:m * kk].reshape(m, kk)
+
+
+def dmrgc_test_svd_gram(precision: int, g: np.ndarray, chi: int, rel_cut: float):
+    """Gram-eigensolver truncated SVD of g (m x n) on the device (diagnostic
+    entry point).  Returns (s, k, U_k); k = -1 and U_k = None when the kept
+    eigenvalues are not resolved."""
+    m, n = g.shape
+    gc = np.asfortranarray(g, dtype=np.complex128)
+    s = np.zeros(m)
+    k = C.c_int()
+    u = np.zeros((m, chi), dtype=np.complex128)
+    _check(lib().dmrgc_test_svd_gram(precision, m, n, gc.ctypes.data, chi, rel_cut, s.ctypes.data,
+                                     C.byref(k), u.ctypes.data))
+    kk = k.value
+    if kk < 0:
+        return s, kk, None
     return s, kk, u.reshape(-1)[:m * kk].reshape(m, kk)
 
 
@@ -383,6 +420,11 @@ def dmrgc_set_jacobi_kernel(variant: int) -> None:
     _check(lib().dmrgc_set_jacobi_kernel(int(variant)))
 
 
+def dmrgc_set_wait_limit(spins: int) -> None:
+    """Iteration limit of the Jacobi kernels' spin waits on the current device (0 = default)."""
+    _check(lib().dmrgc_set_wait_limit(int(spins)))
+
+
 class Context:
     """Owning handle around the C context (marshalling only)."""
 
@@ -418,6 +460,12 @@ class Context:
 
     def get_mps(self):
         return dmrgc_get_mps(self.h, self.n)
+
+    def set_mps(self, mps, log_ft: float = 0.0):
+        dmrgc_set_mps(self.h, mps, log_ft)
+
+    def sweep_updates(self, n_updates: int) -> float:
+        return dmrgc_sweep_updates(self.h, n_updates)
 
     def history(self):
         return dmrgc_step_history(self.h)

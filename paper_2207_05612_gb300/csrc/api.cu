@@ -56,6 +56,9 @@ struct dmrgc_ctx {
   std::vector<char> xyk;
   DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
   DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d, tcerr;
+  DevBuf ovl[2];   // ping-pong environments of dmrgc_overlap (never the sweep's envL / envR)
+  DevBuf ework;    // work space of the Gram eigensolver path (eig_truncate)
+  DevBuf rv[3];    // read-outs: running rows V, site products W = V A_i, T = W E_i
   TcWork tcw;
   // randomized SVD and the rank model (svd_mode 1, 2)
   DevBuf rs_om, rs_y, rs_q, rs_b, rs_h, rs_w, feat, mlp_w, mlp_out, lab;
@@ -195,8 +198,9 @@ cudaError_t run_gemm(int precision, const GemmArgs& g, TcWork* w, int* err_dev, 
   return gemm_simt(g, precision == DMRGC_FP64, st);
 }
 
-dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
-  const bool tc = c->opt.precision == DMRGC_BF16X3 || c->opt.precision == DMRGC_TF32X3;
+dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g, int precision = -1) {
+  if (precision < 0) precision = c->opt.precision;
+  const bool tc = precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3;
   if (tc && !c->tcerr.p) {
     TRY(ensure(c, c->tcerr, 64));
     CK(cudaMemsetAsync(c->tcerr.p, 0, 64, c->st));
@@ -204,7 +208,7 @@ dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g) {
   const double fl = 8.0 * g.M * (double)g.N * g.K * g.b1 * g.b2;
   Span sp(c, TC_GEMM, fl);
   int launches = 0;
-  CK(run_gemm(c->opt.precision, g, &c->tcw, (int*)c->tcerr.p, c->st, &launches));
+  CK(run_gemm(precision, g, &c->tcw, (int*)c->tcerr.p, c->st, &launches));
   c->stats.gemm_launches++;
   c->stats.kernel_launches += launches;
   return DMRGC_OK;
@@ -306,6 +310,82 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
   f = tr.f;
   if (nnz) *nnz = tr.nnz;
   if (norm2) *norm2 = tr.norm2;
+  return DMRGC_OK;
+}
+
+// ---- truncated SVD through the Gram matrix's eigenproblem (complex64 modes)
+//
+// The kept singular vectors of G (rows x kdim, row-major; conj = true: G is
+// conj(theta) read column-wise, i.e. the kept vectors are those of theta^+)
+// are the leading eigenvectors of H = G G^+, formed by the contraction
+// engine with TF32x3 split products (FP32 CUDA cores in the FP32 mode), then
+// diagonalised by eig_truncate.  done = false when the kept eigenvalues are not
+// all resolved above the Gram's rounding level (or the path does not apply):
+// the caller then runs the Jacobi SVD.  out receives the k vectors in layout
+// `mode` (see eig_truncate).
+constexpr double kEigResolve = 1e-4;   // lambda_{k-1} >= 1e-4 lambda_0, i.e. s_{k-1} >= 1e-2 s_1
+constexpr int kEigMinN = 128;
+
+bool eig_applies(const dmrgc_ctx* c, int rows) {
+  return !c->fp64 && c->opt.svd_path == 0 && rows >= kEigMinN && rows <= 2048 && c->chi < rows;
+}
+
+dmrgc_status eig_try(dmrgc_ctx* c, const void* G, int rows, int kdim, bool conj_cols, double cut, double tie,
+                     DevBuf& out, int mode, int& k, bool& done) {
+  done = false;
+  if (!eig_applies(c, rows)) return DMRGC_OK;
+  TRY(ensure(c, c->jw, (size_t)rows * rows * c->esz));
+  GemmArgs g;   // H[r1][r2] = sum_x G[r1][x] conj(G[r2][x])
+  g.M = rows; g.N = rows; g.K = kdim;
+  if (!conj_cols) {
+    g.A = G; g.lda = kdim; g.opA = OP_N;
+    g.B = G; g.ldb = kdim; g.opB = OP_C;
+  } else {        // G = theta^+ with theta [kdim][rows]: H = theta^+ theta
+    g.A = G; g.lda = rows; g.opA = OP_C;
+    g.B = G; g.ldb = rows; g.opB = OP_N;
+  }
+  g.C = c->jw.p; g.ldc = rows;
+  const int gp = c->opt.precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3;
+  TRY(gemm(c, g, gp));
+  const int kk = std::min(c->chi + 1, rows);
+  TRY(ensure(c, c->ework, eig_work_bytes(rows, kk)));
+  TRY(ensure(c, c->tres, trunc_bytes(rows)));
+  TRY(ensure(c, out, (size_t)rows * std::min(c->chi, rows) * c->esz));
+  {
+    Span sp(c, TC_SVD);
+    int launches = 0;
+    CK(eig_truncate(c->jw.p, rows, c->chi, cut, tie, kEigResolve, c->ework.p, c->tres.p, out.p, mode, c->st,
+                    &launches));
+    c->stats.svd_launches += launches;
+    c->stats.kernel_launches += launches;
+  }
+  TruncResult tr{};
+  CK(cudaMemcpyAsync(&tr, c->tres.p, sizeof(tr), cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  if (tr.status == DMRGC_ETIMEOUT) return fail(c, DMRGC_ETIMEOUT, "Gram eigensolver grid barrier timed out");
+  if (tr.status == DMRGC_ENUMERIC) return fail(c, DMRGC_ENUMERIC, "Gram eigensolver met a zero or non-finite spectrum");
+  if (tr.status != 0) {   // 1: not resolved, 2: a non-finite value: the Jacobi SVD decides
+    c->stats.eig_fallbacks++;
+    return DMRGC_OK;
+  }
+  k = tr.k;
+  done = true;
+  c->stats.eig_svds++;
+  c->stats.svd_flops += 16.0 / 3.0 * (double)rows * rows * rows + 8.0 * (double)rows * rows * k;
+  return DMRGC_OK;
+}
+
+// f = |A|^2 of the unnormalised block just formed, then A /= sqrt(f)
+dmrgc_status normalise_block(dmrgc_ctx* c, void* A, long long elems, double& f) {
+  TRY(ensure(c, c->scal, 64));
+  {
+    Span sp(c, TC_OTHER);
+    CK(norm2_scale(A, elems, (double*)c->scal.p, true, c->st));
+    c->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(&f, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  if (!(f > 0) || !std::isfinite(f)) return fail(c, DMRGC_ENUMERIC, "update kept a zero or non-finite weight");
   return DMRGC_OK;
 }
 
@@ -565,21 +645,26 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   bool sketched = false;
   TRY(sketch_size(c, i, mrow, ncol, l));
   if (l > 0) TRY(rsvd_try(c, i, false, mrow, ncol, l, sketched, k, f));
+  bool eig = false;
   if (sketched) {
     TRY(record_end(c, i, k, false, rec));
   } else {
-    TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    {
-      Span sp(c, TC_OTHER);
-      CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
+    // U_k: leading eigenvectors of theta theta^+ where they are resolved, else Jacobi
+    TRY(eig_try(c, c->theta.p, mrow, ncol, false, c->sweep_cut, 0.0, c->A[i], 0, k, eig));
+    if (!eig) {
+      TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+      {
+        Span sp(c, TC_OTHER);
+        CK(copy_transpose(c->theta.p, mrow, ncol, false, c->jw.p, c->fp64, c->st));
+        c->stats.kernel_launches++;
+      }
+      TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
+      TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
-    TRY(svd_columns(c, mrow, ncol, c->sweep_cut, false, 0.0, k, f, &nnz));
     TRY(record_end(c, i, k, true, rec));
-    TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
-    Span sp(c, TC_SVD);
-    CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
-    c->stats.kernel_launches++;
   }
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
   GemmArgs g;   // A_{i+1} = A_i^+ theta / |S_k|
@@ -587,8 +672,13 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
   g.A = c->A[i].p; g.lda = k; g.opA = OP_C;
   g.B = c->theta.p; g.ldb = ncol; g.opB = OP_N;
   g.C = c->A[i + 1].p; g.ldc = ncol;
-  g.alpha_re = 1.0 / std::sqrt(f);
+  // complex64 modes: f = |U_k^+ theta|^2 of the vectors as stored (the kept weight
+  // of the basis actually used, exact up to one FP64 sum), then normalise; FP64
+  // mode: f = sum of the kept s^2 from the SVD
+  const bool renorm = eig || !c->fp64;
+  g.alpha_re = renorm ? 1.0 : 1.0 / std::sqrt(f);
   TRY(gemm(c, g));
+  if (renorm) TRY(normalise_block(c, c->A[i + 1].p, (long long)k * ncol, f));
   c->chiA[i + 1] = k;
   // L_i = A_i^+ X_i
   const int kdim = c->D[i + 1] * c->chiB[i + 1];
@@ -622,22 +712,27 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   bool sketched = false;
   TRY(sketch_size(c, i, mrow, ncol, l));
   if (l > 0) TRY(rsvd_try(c, i, true, mrow, ncol, l, sketched, k, f));
+  bool eig = false;
   if (sketched) {
     TRY(record_end(c, i, k, false, rec));
   } else {
-    TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
-    {
-      Span sp(c, TC_OTHER);
-      CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
+    // V_k^+: leading eigenvectors of theta^+ theta (conjugated rows) where resolved, else Jacobi
+    TRY(eig_try(c, c->theta.p, ncol, mrow, true, c->sweep_cut, 0.0, c->A[i + 1], 2, k, eig));
+    if (!eig) {
+      TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
+      {
+        Span sp(c, TC_OTHER);
+        CK(copy_conj(c->theta.p, (long long)mrow * ncol, c->jw.p, c->fp64, c->st));
+        c->stats.kernel_launches++;
+      }
+      // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
+      TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
+      TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
+      Span sp(c, TC_SVD);
+      CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
-    // columns of theta^+ (column-major == conj(theta) row-major): ncol rows, mrow columns
-    TRY(svd_columns(c, ncol, mrow, c->sweep_cut, false, 0.0, k, f, &nnz));
     TRY(record_end(c, i, k, true, rec));
-    TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
-    Span sp(c, TC_SVD);
-    CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
-    c->stats.kernel_launches++;
   }
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
   GemmArgs g;   // A_i = theta A_{i+1}^+ / |S_k|
@@ -645,8 +740,10 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
   g.A = c->theta.p; g.lda = ncol; g.opA = OP_N;
   g.B = c->A[i + 1].p; g.ldb = ncol; g.opB = OP_C;
   g.C = c->A[i].p; g.ldc = k;
-  g.alpha_re = 1.0 / std::sqrt(f);
+  const bool renorm = eig || !c->fp64;   // as in update_ltr
+  g.alpha_re = renorm ? 1.0 : 1.0 / std::sqrt(f);
   TRY(gemm(c, g));
+  if (renorm) TRY(normalise_block(c, c->A[i].p, (long long)mrow * k, f));
   c->chiA[i + 1] = k;
   const int kdim = c->D[i + 1] * c->chiB[i + 1];
   TRY(ensure(c, c->envR, (size_t)k * kdim * c->esz));
@@ -701,12 +798,14 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
       L.p = c->XY[i].p; L.a = r; L.w = c->D[i + 1]; L.b = c->chiB[i + 1];
       continue;
     }
-    TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
     int k;
     double f;
-    TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
-    TRY(ensure(c, c->A[i], (size_t)r * k * c->esz));
-    {
+    bool eig = false;
+    TRY(eig_try(c, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 0, k, eig));
+    if (!eig) {
+      TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
+      TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
+      TRY(ensure(c, c->A[i], (size_t)r * k * c->esz));
       Span sp(c, TC_SVD);
       CK(gather_columns(c->jw.p, r, r, k, c->tres.p, true, 0, c->A[i].p, c->fp64, c->st));
       c->stats.kernel_launches++;
@@ -735,12 +834,14 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
       R.p = c->XY[i].p; R.a = r; R.w = c->D[i]; R.b = c->chiB[i];
       continue;
     }
-    TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
     int k;
     double f;
-    TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
-    TRY(ensure(c, c->A[i], (size_t)k * r * c->esz));
-    {
+    bool eig = false;
+    TRY(eig_try(c, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 1, k, eig));
+    if (!eig) {
+      TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
+      TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
+      TRY(ensure(c, c->A[i], (size_t)k * r * c->esz));
       Span sp(c, TC_SVD);
       CK(gather_columns(c->jw.p, r, r, k, c->tres.p, true, 1, c->A[i].p, c->fp64, c->st));
       c->stats.kernel_launches++;
@@ -1005,6 +1106,23 @@ dmrgc_status build_mpo(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
   return DMRGC_OK;
 }
 
+// the next `total` updates of the bouncing schedule (Sec. IV.B), then a sync
+dmrgc_status run_updates(dmrgc_ctx* c, long long total) {
+  for (long long u = 0; u < total; ++u) {
+    if (c->N < 2) break;
+    if (c->bond < 0) { c->bond = 0; c->dir = +1; }
+    const int b = c->bond;
+    if (c->dir < 0) {
+      TRY(update_rtl(c, b));
+      if (b == 0) c->dir = +1; else c->bond = b - 1;
+    } else {
+      TRY(update_ltr(c, b));
+      if (b == c->N - 2) c->dir = -1; else c->bond = b + 1;
+    }
+  }
+  return sync(c);
+}
+
 }  // namespace
 
 dmrgc_ctx::~dmrgc_ctx() {
@@ -1012,7 +1130,8 @@ dmrgc_ctx::~dmrgc_ctx() {
   for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &Wc})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
-                    &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr})
+                    &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr,
+                    &ovl[0], &ovl[1], &ework, &rv[0], &rv[1], &rv[2]})
     fr(*b);
   tcw.release();
   for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -1259,19 +1378,7 @@ dmrgc_status dmrgc_sweep(dmrgc_ctx* c, int n_sweeps, double* f_last) {
   if (!c) return DMRGC_EINVAL;
   if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep before dmrgc_apply_layer");
   if (n_sweeps < 0) return fail(c, DMRGC_EINVAL, "n_sweeps < 0");
-  const long long total = (long long)n_sweeps * (c->N - 1);
-  for (long long u = 0; u < total; ++u) {
-    if (c->bond < 0) { c->bond = 0; c->dir = +1; }
-    const int b = c->bond;
-    if (c->dir < 0) {
-      TRY(update_rtl(c, b));
-      if (b == 0) c->dir = +1; else c->bond = b - 1;
-    } else {
-      TRY(update_ltr(c, b));
-      if (b == c->N - 2) c->dir = -1; else c->bond = b + 1;
-    }
-  }
-  TRY(sync(c));
+  TRY(run_updates(c, (long long)n_sweeps * (c->N - 1)));
   if (f_last) *f_last = c->f_cur;
   return DMRGC_OK;
 }
@@ -1291,21 +1398,28 @@ static std::vector<DevBuf>& current_state(dmrgc_ctx* c, std::vector<int>*& bonds
   return c->B;
 }
 
-static dmrgc_status upload_tables(dmrgc_ctx* c, std::vector<DevBuf>& st, const std::vector<int>& bonds,
-                                  int& maxb) {
-  const int N = c->N;
-  std::vector<const void*> ptrs(N);
-  for (int i = 0; i < N; ++i) ptrs[i] = st[i].p;
-  std::vector<int> bt(bonds.begin(), bonds.end());
-  maxb = *std::max_element(bt.begin(), bt.end());
-  bt.push_back(maxb);
-  TRY(ensure(c, c->ptrs_d, sizeof(void*) * 2 * N));
-  TRY(ensure(c, c->bonds_d, sizeof(int) * (N + 2)));
-  TRY(ensure(c, c->order_d, sizeof(int) * N));
-  CK(cudaMemcpyAsync(c->ptrs_d.p, ptrs.data(), sizeof(void*) * N, cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->bonds_d.p, bt.data(), sizeof(int) * (N + 2), cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemcpyAsync(c->order_d.p, c->order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
-  return DMRGC_OK;
+// ---- batched read-outs: per site one GEMM W = V A_i for a chunk of strings
+// (each site tensor read once per chunk), then a select kernel per row.  The
+// GEMMs run in FP64 (FP64 mode), FP32 CUDA cores (FP32 mode) or TF32x3 on the
+// tensor cores (both split modes: their finer split keeps the 54-site product
+// within ~1e-5 relative).
+int readout_precision(const dmrgc_ctx* c) {
+  if (c->fp64) return DMRGC_FP64;
+  return c->opt.precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3;
+}
+
+int readout_chunk(const dmrgc_ctx* c, long long count, int maxb) {
+  const long long cap = (256ll << 20) / ((long long)2 * std::max(maxb, 1) * (long long)c->esz);
+  return (int)std::max(1ll, std::min({count, cap, 16384ll}));
+}
+
+dmrgc_status readout_site(dmrgc_ctx* c, const void* Ai, int B, int l, int r) {
+  GemmArgs g;   // W[b][(x c)] = sum_a V[b][a] A_i[a][(x c)]
+  g.M = B; g.N = 2 * r; g.K = l;
+  g.A = c->rv[0].p; g.lda = l; g.opA = OP_N;
+  g.B = Ai; g.ldb = 2 * r; g.opB = OP_N;
+  g.C = c->rv[1].p; g.ldc = 2 * r;
+  return gemm(c, g, readout_precision(c));
 }
 
 dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
@@ -1317,15 +1431,31 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
     if (bits[j] > 1) return fail(c, DMRGC_EINVAL, "bits must be 0 or 1");
   std::vector<int>* bonds;
   auto& st = current_state(c, bonds);
-  int maxb;
-  TRY(upload_tables(c, st, *bonds, maxb));
-  TRY(ensure(c, c->bits_d, (size_t)count * c->N));
+  const int N = c->N;
+  const int maxb = *std::max_element(bonds->begin(), bonds->begin() + N + 1);
+  const int B0 = readout_chunk(c, count, maxb);
+  TRY(ensure(c, c->rv[0], (size_t)B0 * maxb * c->esz));
+  TRY(ensure(c, c->rv[1], (size_t)B0 * 2 * maxb * c->esz));
+  TRY(ensure(c, c->bits_d, (size_t)count * N));
   TRY(ensure(c, c->out_d, (size_t)count * sizeof(double2)));
-  CK(cudaMemcpyAsync(c->bits_d.p, bits, (size_t)count * c->N, cudaMemcpyHostToDevice, c->st));
-  {
+  CK(cudaMemcpyAsync(c->bits_d.p, bits, (size_t)count * N, cudaMemcpyHostToDevice, c->st));
+  for (long long row0 = 0; row0 < count; row0 += B0) {
+    const int B = (int)std::min<long long>(B0, count - row0);
+    const unsigned char* bd = (const unsigned char*)c->bits_d.p + row0 * N;
+    {
+      Span sp(c, TC_OTHER);
+      CK(readout_start(c->rv[0].p, B, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    for (int i = 0; i < N; ++i) {
+      const int l = (*bonds)[i], r = (*bonds)[i + 1];
+      TRY(readout_site(c, st[i].p, B, l, r));
+      Span sp(c, TC_OTHER);
+      CK(amp_select(c->rv[1].p, B, r, bd, N, c->order[i], c->rv[0].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
     Span sp(c, TC_OTHER);
-    CK(amplitudes((const void* const*)c->ptrs_d.p, (const int*)c->bonds_d.p, (const int*)c->order_d.p,
-                  c->N, maxb, (const unsigned char*)c->bits_d.p, count, (double2*)c->out_d.p, c->fp64, c->st));
+    CK(amp_store(c->rv[0].p, B, (double2*)c->out_d.p + row0, c->fp64, c->st));
     c->stats.kernel_launches++;
   }
   CK(cudaMemcpyAsync(out_re_im, c->out_d.p, (size_t)count * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
@@ -1343,9 +1473,12 @@ dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
   auto& sb = current_state(b, bb);
   if (b->st != a->st) CK(cudaStreamSynchronize(b->st));   // b's tensors are read on a's stream
   const size_t es = a->esz;
-  // E[alpha][beta] over the bonds of a and b, from the left: E <- A_i^+ (E B_i)
+  // E[alpha][beta] over the bonds of a and b, from the left: E <- A_i^+ (E B_i).
+  // The ping-pong buffers are a's own overlap scratch: envL / envR hold the
+  // running sweep environments (c->L, c->R point into them), which a later
+  // dmrgc_sweep on a still reads.
   const void* e_in = a->one.p;
-  DevBuf* bufs[2] = {&a->envL, &a->envR};
+  DevBuf* bufs[2] = {&a->ovl[0], &a->ovl[1]};
   for (int i = 0; i < a->N; ++i) {
     const int la = (*ba)[i], ra = (*ba)[i + 1], lb = (*bb)[i], rb = (*bb)[i + 1];
     TRY(ensure(a, a->T, (size_t)la * 2 * rb * es));
@@ -1381,7 +1514,9 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
   dmrgc_ctx* c = a;   // errors are reported on a
   if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64)
     return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid and storage precision");
-  // the middle section's MPO lives in a scratch context on a's stream
+  // the middle section's MPO lives in a scratch context on a's stream: o keeps
+  // a's cuda_stream, so m->st == a->st and every ensure(m, ...) that grows a
+  // buffer synchronises the stream the GEMMs below run on
   dmrgc_options o = a->opt;
   o.mpo_compress = 0;
   o.svd_mode = 0;
@@ -1391,6 +1526,7 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
   dmrgc_status st = dmrgc_create(a->N, &grid, 1, &o, &m);
   if (st != DMRGC_OK) return fail(a, st, "overlap: scratch context");
   struct Guard { dmrgc_ctx* p; ~Guard() { dmrgc_destroy(p); } } guard{m};
+  if (m->st != a->st) return fail(a, DMRGC_ESTATE, "overlap: scratch context on another stream");
   st = build_mpo(m, gates, n_gates);
   if (st != DMRGC_OK) return fail(a, st, std::string("overlap: ") + m->err);
   if (b->st != a->st) CK(cudaStreamSynchronize(b->st));
@@ -1463,7 +1599,7 @@ dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed
       g.A = An; g.lda = b; g.opA = OP_N;
       g.B = c->E[i + 1].p; g.ldb = b; g.opB = OP_N;
       g.C = c->T.p; g.ldc = b;
-      TRY(gemm(c, g));
+      TRY(gemm(c, g, readout_precision(c)));
       Tsrc = c->T.p;
     }
     GemmArgs h;   // E_i[a][a'] = sum_{(s b)} T[a][(s b)] conj(A_{i+1}[a'][(s b)])
@@ -1471,20 +1607,40 @@ dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed
     h.A = Tsrc; h.lda = 2 * b; h.opA = OP_N;
     h.B = An; h.ldb = 2 * b; h.opB = OP_C;
     h.C = c->E[i].p; h.ldc = a;
-    TRY(gemm(c, h));
+    TRY(gemm(c, h, readout_precision(c)));
     eptr[i] = c->E[i].p;
   }
-  int maxb;
-  TRY(upload_tables(c, st, *bonds, maxb));
-  CK(cudaMemcpyAsync((char*)c->ptrs_d.p + sizeof(void*) * N, eptr.data(), sizeof(void*) * N,
-                     cudaMemcpyHostToDevice, c->st));
+  const int maxb = *std::max_element(bonds->begin(), bonds->begin() + N + 1);
+  const int B0 = readout_chunk(c, count, maxb);
+  TRY(ensure(c, c->rv[0], (size_t)B0 * maxb * c->esz));
+  TRY(ensure(c, c->rv[1], (size_t)B0 * 2 * maxb * c->esz));
+  if (centre > 0) TRY(ensure(c, c->rv[2], (size_t)B0 * 2 * maxb * c->esz));
   TRY(ensure(c, c->bits_d, (size_t)count * N));
-  {
-    Span sp(c, TC_OTHER);
-    CK(sample_bits((const void* const*)c->ptrs_d.p, (const void* const*)c->ptrs_d.p + N,
-                   (const int*)c->bonds_d.p, (const int*)c->order_d.p, N, centre, maxb, seed, count,
-                   (unsigned char*)c->bits_d.p, c->fp64, c->st));
-    c->stats.kernel_launches++;
+  for (long long row0 = 0; row0 < count; row0 += B0) {
+    const int B = (int)std::min<long long>(B0, count - row0);
+    {
+      Span sp(c, TC_OTHER);
+      CK(readout_start(c->rv[0].p, B, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
+    for (int i = 0; i < N; ++i) {
+      const int l = (*bonds)[i], r = (*bonds)[i + 1];
+      TRY(readout_site(c, st[i].p, B, l, r));
+      const void* T = nullptr;
+      if (i < centre) {   // T[(b x)][c'] = sum_c W[(b x)][c] E_i[c][c']
+        GemmArgs g;
+        g.M = 2 * B; g.N = r; g.K = r;
+        g.A = c->rv[1].p; g.lda = r; g.opA = OP_N;
+        g.B = eptr[i]; g.ldb = r; g.opB = OP_N;
+        g.C = c->rv[2].p; g.ldc = r;
+        TRY(gemm(c, g, readout_precision(c)));
+        T = c->rv[2].p;
+      }
+      Span sp(c, TC_OTHER);
+      CK(sample_select(c->rv[1].p, T, B, r, seed, row0, N, i, c->order[i], (unsigned char*)c->bits_d.p,
+                       c->rv[0].p, c->fp64, c->st));
+      c->stats.kernel_launches++;
+    }
   }
   CK(cudaMemcpyAsync(out_bits, c->bits_d.p, (size_t)count * N, cudaMemcpyDeviceToHost, c->st));
   return sync(c);
@@ -1551,6 +1707,48 @@ dmrgc_status dmrgc_get_mps(const dmrgc_ctx* cc, double* out_re_im, int* centre) 
     off += n;
   }
   if (centre) *centre = c->phase == 1 ? c->centre : 0;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_set_mps(dmrgc_ctx* c, const double* in_re_im, const int* bonds, double log_F_tilde) {
+  if (!c) return DMRGC_EINVAL;
+  if (!in_re_im || !bonds) return fail(c, DMRGC_EINVAL, "set_mps: null argument");
+  const int N = c->N;
+  if (bonds[0] != 1 || bonds[N] != 1) return fail(c, DMRGC_EINVAL, "set_mps: outer bonds must be 1");
+  for (int i = 1; i < N; ++i)
+    if (bonds[i] < 1 || bonds[i] > c->chi)
+      return fail(c, DMRGC_EINVAL, "set_mps: bond " + std::to_string(i) + " out of range");
+  for (int i = 0; i < N; ++i)
+    if ((long long)bonds[i] * bonds[i + 1] > (1ll << 26)) return fail(c, DMRGC_EINVAL, "set_mps: site too large");
+  long long off = 0;
+  for (int i = 0; i < N; ++i) {
+    const long long n = 2LL * bonds[i] * bonds[i + 1];
+    TRY(ensure(c, c->B[i], (size_t)n * c->esz));
+    TRY(ensure(c, c->stage_d, (size_t)n * sizeof(double2)));
+    CK(cudaMemcpyAsync(c->stage_d.p, in_re_im + 2 * off, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice,
+                       c->st));
+    CK(from_complex128((const double2*)c->stage_d.p, n, c->fp64, c->B[i].p, c->st));
+    TRY(sync(c));
+    off += n;
+  }
+  c->chiB.assign(bonds, bonds + N + 1);
+  c->chiA = c->chiB;
+  c->phase = 0;
+  c->log_ft = log_F_tilde;
+  c->f_cur = 1.0;
+  c->hist.clear();
+  c->L = EnvRef();
+  c->R = EnvRef();
+  std::fill(c->xyk.begin(), c->xyk.end(), 0);
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_sweep_updates(dmrgc_ctx* c, long long n_updates, double* f_last) {
+  if (!c) return DMRGC_EINVAL;
+  if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep_updates before dmrgc_apply_layer");
+  if (n_updates < 0) return fail(c, DMRGC_EINVAL, "n_updates < 0");
+  TRY(run_updates(c, n_updates));
+  if (f_last) *f_last = c->f_cur;
   return DMRGC_OK;
 }
 
@@ -1642,6 +1840,52 @@ dmrgc_status dmrgc_test_gemm(int precision, int M, int N, int K, int opA, int op
   return cudaDeviceSynchronize() == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
 }
 
+dmrgc_status dmrgc_test_svd_gram(int precision, int m, int n, const double* G, int chi, double rel_cut,
+                                 double* s_out, int* k_out, double* U_out) {
+  if (precision < 1 || precision > 3 || m < 3 || m > 2048 || n < 1 || chi < 1 || chi >= m || !G || !s_out ||
+      !k_out || !U_out)
+    return DMRGC_EINVAL;
+  Scratch s;
+  void* dG;
+  if (upload_as(G, (long long)m * n, false, s, &dG) != cudaSuccess) return DMRGC_ECUDA;
+  void* dH = s.get((size_t)8 * m * m);
+  const int kk = std::min(chi + 1, m);
+  void* work = s.get(eig_work_bytes(m, kk));
+  void* res = s.get(trunc_bytes(m));
+  void* dU = s.get((size_t)8 * m * chi);
+  int* err = (int*)s.get(sizeof(int));
+  if (!dH || !work || !res || !dU || !err || cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return DMRGC_ENOMEM;
+  // G column-major m x n is the row-major [n][m] matrix Gt: H[r1][r2] = sum_c Gt[c][r1] conj(Gt[c][r2])
+  GemmArgs g;
+  g.M = m; g.N = m; g.K = n;
+  g.A = dG; g.lda = m; g.opA = OP_T;
+  g.B = dG; g.ldb = m; g.opB = OP_R;
+  g.C = dH; g.ldc = m;
+  TcWork w;
+  cudaError_t e = run_gemm(precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3, g, &w, err, 0);
+  if (e == cudaSuccess) e = eig_truncate(dH, m, chi, rel_cut, 0.0, 1e-4, work, res, dU, 0, 0, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  w.release();
+  if (e != cudaSuccess) return DMRGC_ECUDA;
+  int herr = 0;
+  TruncResult tr{};
+  if (cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&tr, res, sizeof(tr), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DMRGC_ECUDA;
+  if (herr || tr.status == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;
+  if (tr.status == DMRGC_ENUMERIC) return DMRGC_ENUMERIC;
+  if (cudaMemcpy(s_out, (const char*)res + sizeof(TruncResult), sizeof(double) * m, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return DMRGC_ECUDA;
+  if (tr.status != 0) {
+    *k_out = -1;
+    return DMRGC_OK;
+  }
+  *k_out = tr.k;
+  if (download_from(dU, (long long)m * tr.k, false, s, U_out) != cudaSuccess) return DMRGC_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
+}
+
 dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int chi, double rel_cut,
                             double* s_out, int* k_out, double* U_out) {
   if (precision < 0 || precision > 3 || m < 1 || n < 2 || chi < 1 || !G || !s_out || !k_out || !U_out)
@@ -1671,6 +1915,7 @@ dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int ch
   if (cudaMemcpy(&cs, ctl, sizeof(cs), cudaMemcpyDeviceToHost) != cudaSuccess) return DMRGC_ECUDA;
   if (cs.err == DMRGC_ETIMEOUT) return DMRGC_ETIMEOUT;
   if (cs.err == DMRGC_ENOCONV) return DMRGC_ENOCONV;
+  if (tr.status != 0) return DMRGC_ENUMERIC;
   if (cudaMemcpy(s_out, (const char*)res + sizeof(TruncResult), sizeof(double) * n,
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return DMRGC_ECUDA;

@@ -52,8 +52,9 @@ cudaError_t gemm_simt(const GemmArgs& g, bool fp64, cudaStream_t st);
 // Tensor-core path (complex64 data): packed split operands live in TcWork.
 // err_dev: device int set to DMRGC_ETIMEOUT if a bounded wait ran out.
 struct TcWork {
-  void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
-  size_t cap[4] = {0, 0, 0, 0};
+  // 0-3: packed split operands (A hi, A lo, B hi, B lo); 4: split-K partials
+  void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t cap[5] = {0, 0, 0, 0, 0};
   cudaError_t ensure(int i, size_t bytes);
   void release();
 };
@@ -107,6 +108,20 @@ cudaError_t truncate_columns(const void* W, int m, int n, bool fp64, int chi, do
 // scale_j = s_j (or s_j^2 when squared: Gram input, where the column norm is s^2).
 cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void* res,
                            bool squared, int mode, void* out, bool fp64, cudaStream_t st);
+
+// Truncated SVD through the Gram matrix's eigenproblem (eig_herm.cu), complex64.
+// H: n x n row-major Hermitian (overwritten), 3 <= n <= 2048.  Keeps
+// k = min(chi, n, #{s > cut s_1}) with the multiplet rule of tie_rel (> 0)
+// and writes res (TruncResult + s[n] + perm[n], as truncate_columns) and the
+// k leading eigenvectors to out: mode 0 out[r * k + v], mode 1 out[v * n + r],
+// mode 2 out[v * n + r] conjugated.  res->status: 0 done; 1 not resolved
+// (lambda_{k-1} < resolve * lambda_0 or the count set by the cut: use the
+// Jacobi SVD; nothing is written to out); DMRGC_ENUMERIC; DMRGC_ETIMEOUT.
+size_t eig_work_bytes(int n, int kk);
+cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, double resolve, void* work,
+                         void* res, void* out, int mode, cudaStream_t st, int* launches);
+// |x|^2 (complex64, FP64 sum in a fixed order) to *out_dev; x /= |x| if scale
+cudaError_t norm2_scale(void* x, long long n, double* out_dev, bool scale, cudaStream_t st);
 
 // Spectrum read-outs of a truncation result (k = kept count):
 // out32[j] = log10(s_mu^2 / sum_{nu<k} s_nu^2) at mu = round(j (k-1) / 31), j < 32;
@@ -173,12 +188,20 @@ cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* ds
 
 // --------------------------------------------------------------- read-outs
 
-cudaError_t amplitudes(const void* const* sites, const int* bonds, const int* order, int n_sites,
-                       int max_bond, const unsigned char* bits, long long count, double2* out,
-                       bool fp64, cudaStream_t st);
-cudaError_t sample_bits(const void* const* sites, const void* const* emat, const int* bonds,
-                        const int* order, int n_sites, int centre, int max_bond,
-                        unsigned long long seed, long long count, unsigned char* out, bool fp64,
-                        cudaStream_t st);
+// Batched read-outs (readout.cu), one site at a time, for a chunk of B strings
+// whose running row vectors V[B][l] the caller multiplies by the site tensor
+// (W[B][2 r] = V A_i, the contraction engine) before each call:
+//  readout_start: V[b][0] = 1;
+//  amp_select:    V[b][c] = W[b][x_b r + c], x_b = bits[b * n + qubit];
+//  sample_select: draws bit x of sample row0 + b at `site` from p_x = |W_x|^2
+//                 (T = null) or Re <T_x, W_x> (T = W E, left of the centre),
+//                 out[(row0 + b) * n + qubit] = x, V[b] = W_x / sqrt(p_x);
+//  amp_store:     out[b] = V[b][0] as complex128.
+cudaError_t readout_start(void* V, int B, bool fp64, cudaStream_t st);
+cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, int qubit, void* V, bool fp64,
+                       cudaStream_t st);
+cudaError_t sample_select(const void* W, const void* T, int B, int r, unsigned long long seed, long long row0, int n,
+                          int site, int qubit, unsigned char* out, void* V, bool fp64, cudaStream_t st);
+cudaError_t amp_store(const void* V, int B, double2* out, bool fp64, cudaStream_t st);
 
 }  // namespace dmrgc

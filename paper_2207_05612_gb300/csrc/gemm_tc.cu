@@ -17,7 +17,9 @@
 // blocks of A_hi, A_lo, B_hi, B_lo with TMA (128-byte swizzle, K-major) into a
 // 2-stage ring; warp 1 (one thread) issues 3 x (BK / MMA_K) MMAs per stage and
 // frees the stage with tcgen05.commit; all 4 warps then read TMEM
-// (32 lanes x 32 columns per load) and write or atomically add complex C.
+// (32 lanes x 32 columns per load) and write complex C.  With split-K each
+// split writes its partial product to a workspace and one more kernel sums the
+// partials in a fixed order (no atomics), so every product is reproducible.
 // Every mbarrier wait is bounded by the global timer; an exhausted wait sets
 // an error flag, stops issuing, drains what is in flight (bounded), frees TMEM
 // and returns.
@@ -25,6 +27,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -50,7 +53,8 @@ struct TcArgs {
   float2* C;
   long long ldc, sC1, sC2;
   float alpha_re, alpha_im;
-  int mode;            // 0 store, 1 add to C (beta = 1), 2 atomic add (split-K)
+  int mode;            // 0 store, 1 add to C (beta = 1), 2 split-K partial into P
+  float2* P;           // split-K partials [split][batch][M][N] (mode 2)
   int* err;
 };
 
@@ -270,8 +274,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float vr = re * g.alpha_re - im * g.alpha_im;
             const float vi = re * g.alpha_im + im * g.alpha_re;
             if (g.mode == 2) {
-              atomicAdd(&dst[j].x, vr);
-              atomicAdd(&dst[j].y, vi);
+              float2* pd = g.P + ((long long)ks * (gridDim.z / g.split) + batch) * ((long long)g.M * g.N) +
+                           (long long)row * g.N + ncol0;
+              pd[j] = make_float2(vr, vi);
             } else if (g.mode == 1) {
               float2 o = dst[j];
               dst[j] = make_float2(o.x + vr, o.y + vi);
@@ -391,12 +396,29 @@ __global__ void pack_kernel(const float2* __restrict__ src, long long ld, long l
   }
 }
 
-__global__ void zero_c_kernel(float2* C, int M, int N, long long ldc, long long s1, long long s2, int b2) {
+// split-K reduction in a fixed order (partial 0 first), so that a product is
+// the same bit for bit from run to run: C (+)= sum_s P[s][batch]
+__global__ void splitk_reduce_kernel(const float2* __restrict__ P, int split, int nbatch, float2* C, int M, int N,
+                                     long long ldc, long long s1, long long s2, int b2, int beta_one) {
   const int batch = blockIdx.z;
   float2* Cb = C + (long long)(batch / b2) * s1 + (long long)(batch % b2) * s2;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * N;
-       e += (long long)gridDim.x * blockDim.x)
-    Cb[(e / N) * ldc + (e % N)] = make_float2(0.f, 0.f);
+  const long long mn = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn;
+       e += (long long)gridDim.x * blockDim.x) {
+    float2 acc = P[(long long)batch * mn + e];
+    for (int s = 1; s < split; ++s) {
+      const float2 v = P[((long long)s * nbatch + batch) * mn + e];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    float2* dst = Cb + (e / N) * ldc + (e % N);
+    if (beta_one) {
+      const float2 o = *dst;
+      acc.x = o.x + acc.x;
+      acc.y = o.y + acc.y;
+    }
+    *dst = acc;
+  }
 }
 
 // ---- host side
@@ -495,20 +517,30 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
     if (split < 1) split = 1;
   }
   if ((long long)g.b1 * g.b2 * split > 65535) split = 1;
-  a.split = split;
   a.per = (a.ktiles + split - 1) / split;
+  split = (a.ktiles + a.per - 1) / a.per;   // every split owns at least one K block
+  a.split = split;
   a.mode = split > 1 ? 2 : (g.beta_one ? 1 : 0);
-  if (launches) *launches = 3 + (split > 1 && !g.beta_one ? 1 : 0);
-  if (split > 1 && !g.beta_one) {
-    dim3 zg(64, 1, (unsigned)(g.b1 * g.b2));
-    zero_c_kernel<<<zg, 256, 0, st>>>((float2*)g.C, g.M, g.N, g.ldc, g.sC1, g.sC2, g.b2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nbatch = g.b1 * g.b2;
+  if (split > 1) {
+    if ((e = w.ensure(4, (size_t)split * nbatch * g.M * g.N * sizeof(float2))) != cudaSuccess) return e;
+    a.P = (float2*)w.buf[4];
   }
+  if (launches) *launches = 3 + (split > 1 ? 1 : 0);
   if ((e = allow_dyn_smem((const void*)tc_gemm_kernel<ESZ>)) != cudaSuccess) return e;
-  dim3 grid((2 * g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM, (unsigned)(g.b1 * g.b2 * split));
+  dim3 grid((2 * g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM, (unsigned)(nbatch * split));
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   tc_gemm_kernel<ESZ><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(tAh, tAl, tBh, tBl, a);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (split > 1) {
+    const long long mn = (long long)g.M * g.N;
+    int bx = (int)std::min<long long>((mn + 255) / 256, 1024);
+    dim3 rg(bx < 1 ? 1 : bx, 1, (unsigned)nbatch);
+    splitk_reduce_kernel<<<rg, 256, 0, st>>>(a.P, split, nbatch, (float2*)g.C, g.M, g.N, g.ldc, g.sC1, g.sC2, g.b2,
+                                             g.beta_one);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace
@@ -533,7 +565,7 @@ cudaError_t TcWork::ensure(int i, size_t bytes) {
 }
 
 void TcWork::release() {
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
     if (buf[i]) cudaFree(buf[i]);
     buf[i] = nullptr;
     cap[i] = 0;

@@ -1,7 +1,7 @@
 // Read-outs of the MPS: amplitudes <x|Psi> and bit-string sampling.
 //
 // Amplitude (Sec. IV.A, the MPS definition): <x|Psi> = A_1[x_1] ... A_N[x_N],
-// one CTA per bit string, the running row vector kept in shared memory.
+// for a chunk of strings at once, site by site.
 // Sampling: sequential conditional sampling.  With the orthogonality centre on
 // site c, the norm of any continuation of the prefix x_<=i is v E_i v^+ where
 // v = A_1[x_1]..A_i[x_i] and E_i is the norm matrix of sites > i (identity for
@@ -33,145 +33,121 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Batched read-outs.  Per site i the running row vectors of a chunk of B
+// strings, V[B][l], are multiplied by the whole site tensor as one GEMM
+// (W[b][x r + c] = sum_a V[b][a] A_i[a][x][c], done by the contraction engine
+// before this kernel), so every site tensor is read once per chunk instead of
+// once per string.  The kernels below take one row per CTA and pick x.
+
+// amplitudes: V'[b][c] = W[b][x_b r + c], x_b the string's bit at site i
 template <typename C2>
-__global__ void amp_kernel(const void* const* __restrict__ sites, const int* __restrict__ bonds,
-                           const int* __restrict__ order, int n, const unsigned char* __restrict__ bits,
-                           long long count, double2* __restrict__ out) {
-  extern __shared__ double2 sv[];   // [2][max_bond]
-  const long long j = blockIdx.x;
-  if (j >= count) return;
-  double2* v = sv;
-  const int maxb = bonds[n + 1];
-  double2* w = sv + maxb;
-  if (threadIdx.x == 0) v[0] = double2{1.0, 0.0};
-  __syncthreads();
-  for (int i = 0; i < n; ++i) {
-    const int l = bonds[i], r = bonds[i + 1];
-    const int x = bits[j * n + order[i]];
-    const C2* A = reinterpret_cast<const C2*>(sites[i]);
-    for (int b = threadIdx.x; b < r; b += blockDim.x) {
-      double2 acc{0, 0};
-      for (int a = 0; a < l; ++a) {
-        const C2 t = A[((long long)a * 2 + x) * r + b];
-        const double2 tv{(double)t.x, (double)t.y};
-        acc = cadd(acc, cmul(v[a], tv));
-      }
-      w[b] = acc;
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < r; b += blockDim.x) v[b] = w[b];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[j] = v[0];
+__global__ void amp_select_kernel(const C2* __restrict__ W, int r, const unsigned char* __restrict__ bits,
+                                  int n, int qubit, C2* __restrict__ V) {
+  const int b = blockIdx.x;
+  const int x = bits[(long long)b * n + qubit];
+  const C2* src = W + (long long)b * 2 * r + (long long)x * r;
+  C2* dst = V + (long long)b * r;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) dst[c] = src[c];
 }
 
+// sampling: p_x = |W_x|^2 (site at or right of the centre, T = null) or
+// Re sum_c T[b][x r + c] conj(W[b][x r + c]) with T = W E_i (left of it);
+// bit 0 iff u < p_0 / (p_0 + p_1), u = SplitMix64 at counter j N + i for
+// global sample j = row0 + b; V'[b] = W_x[b] / sqrt(p_x).
 template <typename C2>
-__global__ void sample_kernel(const void* const* __restrict__ sites, const void* const* __restrict__ emat,
-                              const int* __restrict__ bonds, const int* __restrict__ order, int n,
-                              int centre, unsigned long long seed, long long count,
-                              unsigned char* __restrict__ out) {
-  extern __shared__ double2 sm[];   // v, w0, w1 [max_bond each], red[32]
-  const long long j = blockIdx.x;
-  if (j >= count) return;
-  const int maxb = bonds[n + 1];
-  double2* v = sm;
-  double2* w0 = sm + maxb;
-  double2* w1 = sm + 2 * maxb;
-  double* red = reinterpret_cast<double*>(sm + 3 * maxb);
-  if (threadIdx.x == 0) v[0] = double2{1.0, 0.0};
-  __syncthreads();
-  for (int i = 0; i < n; ++i) {
-    const int l = bonds[i], r = bonds[i + 1];
-    const C2* A = reinterpret_cast<const C2*>(sites[i]);
-    for (int b = threadIdx.x; b < r; b += blockDim.x) {
-      double2 a0{0, 0}, a1{0, 0};
-      for (int a = 0; a < l; ++a) {
-        const C2 t0 = A[((long long)a * 2 + 0) * r + b];
-        const C2 t1 = A[((long long)a * 2 + 1) * r + b];
-        a0 = cadd(a0, cmul(v[a], double2{(double)t0.x, (double)t0.y}));
-        a1 = cadd(a1, cmul(v[a], double2{(double)t1.x, (double)t1.y}));
-      }
-      w0[b] = a0;
-      w1[b] = a1;
-    }
-    __syncthreads();
-    double p0 = 0, p1 = 0;
-    if (i >= centre) {
-      for (int b = threadIdx.x; b < r; b += blockDim.x) {
-        p0 += w0[b].x * w0[b].x + w0[b].y * w0[b].y;
-        p1 += w1[b].x * w1[b].x + w1[b].y * w1[b].y;
-      }
+__global__ void sample_select_kernel(const C2* __restrict__ W, const C2* __restrict__ T, int r,
+                                     unsigned long long seed, long long row0, int n, int site, int qubit,
+                                     unsigned char* __restrict__ out, C2* __restrict__ V) {
+  __shared__ double red[32];
+  __shared__ int s_x;
+  __shared__ double s_inv;
+  const int b = blockIdx.x;
+  const C2* w = W + (long long)b * 2 * r;
+  const C2* t = T ? T + (long long)b * 2 * r : nullptr;
+  double p0 = 0, p1 = 0;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    const C2 a0 = w[c], a1 = w[r + c];
+    if (t) {
+      const C2 e0 = t[c], e1 = t[r + c];
+      p0 += (double)e0.x * a0.x + (double)e0.y * a0.y;
+      p1 += (double)e1.x * a1.x + (double)e1.y * a1.y;
     } else {
-      // p = w E w^+ = sum_b w[b] sum_b' E[b][b'] conj(w[b'])
-      const C2* E = reinterpret_cast<const C2*>(emat[i]);
-      for (int b = threadIdx.x; b < r; b += blockDim.x) {
-        double2 e0{0, 0}, e1{0, 0};
-        for (int bb = 0; bb < r; ++bb) {
-          const C2 t = E[(long long)b * r + bb];
-          const double2 tv{(double)t.x, (double)t.y};
-          e0 = cadd(e0, cmul(tv, cconj(w0[bb])));
-          e1 = cadd(e1, cmul(tv, cconj(w1[bb])));
-        }
-        p0 += cmul(w0[b], e0).x;
-        p1 += cmul(w1[b], e1).x;
-      }
+      p0 += (double)a0.x * a0.x + (double)a0.y * a0.y;
+      p1 += (double)a1.x * a1.x + (double)a1.y * a1.y;
     }
-    p0 = block_sum(p0, red);
-    p1 = block_sum(p1, red);
-    const double u = splitmix64_uniform(seed, (unsigned long long)j * n + i);
+  }
+  p0 = block_sum(p0, red);
+  p1 = block_sum(p1, red);
+  if (threadIdx.x == 0) {
+    const long long j = row0 + b;
+    const double u = splitmix64_uniform(seed, (unsigned long long)j * n + site);
     const double tot = p0 + p1;
     const int x = (tot > 0 && u < p0 / tot) ? 0 : 1;
     const double px = x == 0 ? p0 : p1;
-    const double inv = px > 0 ? 1.0 / sqrt(px) : 0.0;
-    const double2* src = x == 0 ? w0 : w1;
-    for (int b = threadIdx.x; b < r; b += blockDim.x) v[b] = double2{src[b].x * inv, src[b].y * inv};
-    if (threadIdx.x == 0) out[j * n + order[i]] = (unsigned char)x;
-    __syncthreads();
+    s_x = x;
+    s_inv = px > 0 ? 1.0 / sqrt(px) : 0.0;
+    out[j * n + qubit] = (unsigned char)x;
   }
+  __syncthreads();
+  const int x = s_x;
+  const double inv = s_inv;
+  const C2* src = w + (long long)x * r;
+  C2* dst = V + (long long)b * r;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    const C2 a = src[c];
+    dst[c] = C2{(decltype(a.x))(a.x * inv), (decltype(a.x))(a.y * inv)};
+  }
+}
+
+template <typename C2>
+__global__ void amp_store_kernel(const C2* __restrict__ V, int B, double2* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) out[b] = double2{(double)V[b].x, (double)V[b].y};
+}
+
+template <typename C2>
+__global__ void ones_kernel(C2* __restrict__ V, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) V[b] = C2{1, 0};
 }
 
 }  // namespace
 
-cudaError_t amplitudes(const void* const* sites, const int* bonds, const int* order, int n_sites,
-                       int max_bond, const unsigned char* bits, long long count, double2* out,
-                       bool fp64, cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
-  if (count > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const size_t sm = 2 * (size_t)max_bond * sizeof(double2);
-  const int threads = max_bond >= 256 ? 256 : 128;
-  cudaError_t e;
-  if (fp64) {
-    e = allow_dyn_smem((const void*)amp_kernel<double2>);
-    if (e != cudaSuccess) return e;
-    amp_kernel<double2><<<(unsigned)count, threads, sm, st>>>(sites, bonds, order, n_sites, bits, count, out);
-  } else {
-    e = allow_dyn_smem((const void*)amp_kernel<float2>);
-    if (e != cudaSuccess) return e;
-    amp_kernel<float2><<<(unsigned)count, threads, sm, st>>>(sites, bonds, order, n_sites, bits, count, out);
-  }
+cudaError_t readout_start(void* V, int B, bool fp64, cudaStream_t st) {
+  if (fp64) ones_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<double2*>(V), B);
+  else ones_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2*>(V), B);
   return cudaGetLastError();
 }
 
-cudaError_t sample_bits(const void* const* sites, const void* const* emat, const int* bonds,
-                        const int* order, int n_sites, int centre, int max_bond,
-                        unsigned long long seed, long long count, unsigned char* out, bool fp64,
-                        cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
-  if (count > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const size_t sm = 3 * (size_t)max_bond * sizeof(double2) + 32 * sizeof(double);
-  const int threads = 256;
-  cudaError_t e;
-  if (fp64) {
-    e = allow_dyn_smem((const void*)sample_kernel<double2>);
-    if (e != cudaSuccess) return e;
-    sample_kernel<double2><<<(unsigned)count, threads, sm, st>>>(sites, emat, bonds, order, n_sites,
-                                                                 centre, seed, count, out);
-  } else {
-    e = allow_dyn_smem((const void*)sample_kernel<float2>);
-    if (e != cudaSuccess) return e;
-    sample_kernel<float2><<<(unsigned)count, threads, sm, st>>>(sites, emat, bonds, order, n_sites,
-                                                                centre, seed, count, out);
-  }
+cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, int qubit, void* V, bool fp64,
+                       cudaStream_t st) {
+  const int threads = r >= 256 ? 256 : (r >= 64 ? 64 : 32);
+  if (fp64)
+    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const double2*>(W), r, bits, n, qubit,
+                                             reinterpret_cast<double2*>(V));
+  else
+    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const float2*>(W), r, bits, n, qubit,
+                                             reinterpret_cast<float2*>(V));
+  return cudaGetLastError();
+}
+
+cudaError_t sample_select(const void* W, const void* T, int B, int r, unsigned long long seed, long long row0, int n,
+                          int site, int qubit, unsigned char* out, void* V, bool fp64, cudaStream_t st) {
+  const int threads = r >= 256 ? 256 : (r >= 64 ? 64 : 32);
+  if (fp64)
+    sample_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const double2*>(W),
+                                                reinterpret_cast<const double2*>(T), r, seed, row0, n, site, qubit,
+                                                out, reinterpret_cast<double2*>(V));
+  else
+    sample_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const float2*>(W),
+                                                reinterpret_cast<const float2*>(T), r, seed, row0, n, site, qubit,
+                                                out, reinterpret_cast<float2*>(V));
+  return cudaGetLastError();
+}
+
+cudaError_t amp_store(const void* V, int B, double2* out, bool fp64, cudaStream_t st) {
+  if (fp64) amp_store_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2*>(V), B, out);
+  else amp_store_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float2*>(V), B, out);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,12 @@ static_assert(offsetof(JacobiCtl, rotations) == offsetof(JacobiStatus, rotations
 
 __device__ __forceinline__ unsigned* block_rounds(JacobiCtl* c) { return reinterpret_cast<unsigned*>(c + 1); }
 
-constexpr unsigned long long kSpinLimit = 20000000ull;  // x ~64 ns = ~1.3 s
+// Iteration limit of every spin wait in the Jacobi kernels (the grid barrier
+// and the per-block round counters): 20M polls of ~64 ns, about 1.3 s.  One
+// copy per device; dmrgc_set_wait_limit changes it (tests make a wait run
+// out with a limit of a few polls, which ends the launch with ETIMEOUT).
+constexpr unsigned long long kSpinLimitDefault = 20000000ull;
+__device__ unsigned long long g_spin_limit = kSpinLimitDefault;
 
 __device__ __forceinline__ bool grid_barrier(JacobiCtl* c, unsigned nblocks) {
   __syncthreads();
@@ -57,10 +62,11 @@ __device__ __forceinline__ bool grid_barrier(JacobiCtl* c, unsigned nblocks) {
       atomicAdd(&c->gen, 1u);
     } else {
       unsigned long long it = 0;
+      const unsigned long long lim = g_spin_limit;
       while (*vgen == g) {
         if (it > 4096) __nanosleep(64);
         if (*verr != 0) break;
-        if (++it > kSpinLimit) {
+        if (++it > lim) {
           atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
           break;
         }
@@ -80,10 +86,11 @@ __device__ __forceinline__ bool wait_rounds(JacobiCtl* c, const unsigned* done, 
     volatile const unsigned* dj = done + J;
     volatile int* verr = &c->err;
     unsigned long long it = 0;
+    const unsigned long long lim = g_spin_limit;
     while (*di < need || *dj < need) {
       if (it > 4096) __nanosleep(64);
       if (*verr != 0) break;
-      if (++it > kSpinLimit) {
+      if (++it > lim) {
         atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
         break;
       }
@@ -167,12 +174,14 @@ __global__ void __launch_bounds__(128) jacobi_kernel(typename cplx<R>::T* __rest
         const R t = -sg / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
         const R c = R(1) / sqrt(R(1) + t * t);
         const R s = c * t;
-        // u' = c u - s e^{-i phi} v ;  v' = s u + c e^{-i phi} v
+        const R mst = -s * (s / (R(1) + c));   // c - 1, accurate when c rounds to 1
+        // u' = c u - s e^{-i phi} v ;  v' = s u + c e^{-i phi} v, as corrections
+        // of the columns themselves (see the column-pair kernel below)
         for (int i = lane; i < m; i += 32) {
           const C2 x = u[i], y = v[i];
           const C2 ye{y.x * er - y.y * ei, y.x * ei + y.y * er};
-          u[i] = C2{c * x.x - s * ye.x, c * x.y - s * ye.y};
-          v[i] = C2{s * x.x + c * ye.x, s * x.y + c * ye.y};
+          u[i] = C2{x.x + (mst * x.x - s * ye.x), x.y + (mst * x.y - s * ye.y)};
+          v[i] = C2{ye.x + (s * x.x + mst * ye.x), ye.y + (s * x.y + mst * ye.y)};
         }
       }
       if (lane == 0 && local_off > 0.f)
@@ -255,13 +264,14 @@ __global__ void __launch_bounds__(128) jacobi_reg_kernel(typename cplx<R>::T* __
         const R t = -sg / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
         const R c = R(1) / sqrt(R(1) + t * t);
         const R sn = c * t;
+        const R mst = -sn * (sn / (R(1) + c));   // c - 1, accurate when c rounds to 1
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int i = tid + e * 128;
           if (i < m) {
             const C2 ye{y[e].x * er - y[e].y * ei, y[e].x * ei + y[e].y * er};
-            u[i] = C2{c * x[e].x - sn * ye.x, c * x[e].y - sn * ye.y};
-            v[i] = C2{sn * x[e].x + c * ye.x, sn * x[e].y + c * ye.y};
+            u[i] = C2{x[e].x + (mst * x[e].x - sn * ye.x), x[e].y + (mst * x[e].y - sn * ye.y)};
+            v[i] = C2{ye.x + (sn * x[e].x + mst * ye.x), ye.y + (sn * x[e].y + mst * ye.y)};
           }
         }
       }
@@ -281,335 +291,6 @@ __global__ void __launch_bounds__(128) jacobi_reg_kernel(typename cplx<R>::T* __
     ctl->sweeps = sweep;
     const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
     if (sweep >= max_sweeps && off > (float)tol && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
-  }
-}
-
-// Blocked variant (complex64, m <= 128*E): the columns form blocks of 4 and
-// the blocks follow the round-robin order.  In a block round a CTA holds two
-// blocks (8 columns) in registers and rotates all 16 cross pairs in 4
-// sub-rounds of 4 disjoint pairs -- plus, in the first block round of a sweep,
-// the 6 intra-block pairs of each of its blocks -- so one grid barrier covers
-// 16 pair rotations and a sweep needs n/4 - 1 barriers instead of n - 1.  Every
-// column pair still meets exactly once per sweep (cyclic Jacobi reordered).
-template <int SUB, int E>
-__device__ __forceinline__ void blk_subround(float2 (&x)[8][E], const bool (&valid)[8], float (&red)[2][4][16],
-                                             int& buf, float tiny, float tol, float& local_off,
-                                             unsigned long long& rot) {
-  // sub-rounds 0-2: intra-block pairs (block I = slots 0..3, block J = slots 4..7);
-  // 3-6: cross pairs, slot q of I with slot (q + s) mod 4 of J
-  constexpr int P[7][4][2] = {{{0, 1}, {2, 3}, {4, 5}, {6, 7}}, {{0, 2}, {1, 3}, {4, 6}, {5, 7}},
-                              {{0, 3}, {1, 2}, {4, 7}, {5, 6}}, {{0, 4}, {1, 5}, {2, 6}, {3, 7}},
-                              {{0, 5}, {1, 6}, {2, 7}, {3, 4}}, {{0, 6}, {1, 7}, {2, 4}, {3, 5}},
-                              {{0, 7}, {1, 4}, {2, 5}, {3, 6}}};
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float acc[4][4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const float2 a = x[P[SUB][k][0]][e], b = x[P[SUB][k][1]][e];
-      al += a.x * a.x + a.y * a.y;
-      be += b.x * b.x + b.y * b.y;
-      gr += a.x * b.x + a.y * b.y;
-      gi += a.x * b.y - a.y * b.x;
-    }
-    acc[k][0] = al; acc[k][1] = be; acc[k][2] = gr; acc[k][3] = gi;
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[k][q] = warp_sum(acc[k][q]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) red[buf][wid][4 * k + q] = acc[k][q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      acc[k][q] = red[buf][0][4 * k + q] + red[buf][1][4 * k + q] + red[buf][2][4 * k + q] + red[buf][3][4 * k + q];
-  buf ^= 1;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int ia = P[SUB][k][0], ib = P[SUB][k][1];
-    if (!valid[ia] || !valid[ib]) continue;
-    const float al = acc[k][0], be = acc[k][1], gr = acc[k][2], gi = acc[k][3];
-    const float gabs = sqrtf(gr * gr + gi * gi);
-    if (al <= tiny || be <= tiny || gabs <= tiny) continue;
-    const float rel = gabs / sqrtf(al * be);
-    if (!(rel > tol)) continue;
-    local_off = fmaxf(local_off, rel);
-    if (threadIdx.x == 0) ++rot;
-    const float er = gr / gabs, ei = -gi / gabs;
-    const float zeta = (al - be) / (2.f * gabs);
-    const float sg = zeta >= 0.f ? 1.f : -1.f;
-    const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-    const float c = 1.f / sqrtf(1.f + t * t);
-    const float sn = c * t;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const float2 xa = x[P[SUB][k][0]][e], yb = x[P[SUB][k][1]][e];
-      const float2 ye{yb.x * er - yb.y * ei, yb.x * ei + yb.y * er};
-      x[P[SUB][k][0]][e] = float2{c * xa.x - sn * ye.x, c * xa.y - sn * ye.y};
-      x[P[SUB][k][1]][e] = float2{sn * xa.x + c * ye.x, sn * xa.y + c * ye.y};
-    }
-  }
-}
-
-template <int E>
-__global__ void __launch_bounds__(128, 2) jacobi_blk_kernel(float2* __restrict__ G, int m, int n, int nblk,
-                                                            float tol, int max_sweeps,
-                                                            const double* __restrict__ fro2, float zero_rel,
-                                                            JacobiCtl* ctl) {
-  __shared__ float red[2][4][16];
-  const int tid = threadIdx.x;
-  const unsigned nb = gridDim.x;
-  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
-  const float tiny = (float)fmax(fz, 1e-30);
-  int sweep = 0, buf = 0;
-  unsigned long long rot = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    float local_off = 0.f;
-    for (int r = 0; r < nblk - 1; ++r) {
-      for (int p = blockIdx.x; p < nblk / 2; p += gridDim.x) {
-        int I, J;
-        round_robin_pair(r, p, nblk, I, J);
-        int col[8];
-        bool valid[8];
-        float2 x[8][E];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          col[q] = (q < 4 ? I : J) * 4 + (q & 3);
-          valid[q] = col[q] < n;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int i = tid + e * 128;
-            x[q][e] = (valid[q] && i < m) ? G[(long long)col[q] * m + i] : float2{0.f, 0.f};
-          }
-        }
-        if (r == 0) {
-          blk_subround<0, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-          blk_subround<1, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-          blk_subround<2, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-        }
-        blk_subround<3, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-        blk_subround<4, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-        blk_subround<5, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-        blk_subround<6, E>(x, valid, red, buf, tiny, tol, local_off, rot);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (!valid[q]) continue;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int i = tid + e * 128;
-            if (i < m) G[(long long)col[q] * m + i] = x[q][e];
-          }
-        }
-      }
-      if (tid == 0 && local_off > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(local_off));
-      local_off = 0.f;
-      if (!grid_barrier(ctl, nb)) {
-        if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
-        return;
-      }
-      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
-    }
-    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
-    if (!(off > tol)) { ++sweep; break; }
-  }
-  if (tid == 0 && rot) atomicAdd(&ctl->rotations, rot);
-  if (blockIdx.x == 0 && tid == 0) {
-    ctl->sweeps = sweep;
-    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
-    if (sweep >= max_sweeps && off > tol && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
-  }
-}
-
-// Warp-pair variant (complex64, m <= 32*E): a CTA of 16 warps holds two
-// blocks of 8 columns, one column per warp in registers (lane l owns rows
-// l, l+32, ...).  In a sub-round the 16 warps form 8 disjoint pairs; the two
-// warps of a pair swap columns through shared memory, each computes the same
-// alpha, beta, gamma with warp shuffles only, and each applies its half of the
-// rotation to its own column.  One grid barrier separates block rounds
-// (column blocks move between CTAs in round-robin order).
-template <int SUB>
-__device__ __forceinline__ int wp_partner(int w) {
-  if (SUB < 7) {
-    // circle method on the 8 slots of each block: slot 0 fixed, slot q >= 1 at
-    // rotation position x = (q - 1 - SUB) mod 7; positions x and 7 - x pair up,
-    // position 0 pairs with slot 0
-    const int blk = w >> 3, q = w & 7;
-    int partner;
-    if (q == 0) {
-      partner = SUB % 7 + 1;
-    } else {
-      const int x = ((q - 1 - SUB) % 7 + 7) % 7;
-      partner = (x == 0) ? 0 : ((7 - x) + SUB) % 7 + 1;
-    }
-    return blk * 8 + partner;
-  }
-  const int s = SUB - 7;   // cross: slot q of block I with slot (q + s) mod 8 of block J
-  return w < 8 ? 8 + ((w + s) & 7) : ((w - 8 - s) & 7);
-}
-
-template <int E>
-__device__ __forceinline__ float warp_allsum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <int SUB, int E>
-__device__ __forceinline__ void wp_subround(float2 (&x)[E], bool valid_me, const bool* valid_all, float2* sbuf,
-                                            int m, float tiny, float tol, float& local_off,
-                                            unsigned long long& rot) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = wp_partner<SUB>(w);
-  const bool first = w < p;                 // the pair's first column is the lower slot
-  // own column to shared memory; the partner's column is then read from there
-  // (twice, so that only one column lives in registers); the closing barrier
-  // keeps the next sub-round from overwriting a column still being read
-  float2* mine = sbuf + (long long)w * m;
-  const float2* theirs = sbuf + (long long)p * m;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = lane + 32 * e;
-    if (i < m) mine[i] = x[e];
-  }
-  __syncthreads();
-  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;   // (u, v) = (first, second) column
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = lane + 32 * e;
-    const float2 y = (i < m) ? theirs[i] : float2{0.f, 0.f};
-    const float2 u = first ? x[e] : y;
-    const float2 v = first ? y : x[e];
-    al += u.x * u.x + u.y * u.y;
-    be += v.x * v.x + v.y * v.y;
-    gr += u.x * v.x + u.y * v.y;
-    gi += u.x * v.y - u.y * v.x;
-  }
-  al = warp_allsum<E>(al);
-  be = warp_allsum<E>(be);
-  gr = warp_allsum<E>(gr);
-  gi = warp_allsum<E>(gi);
-  const float gabs = sqrtf(gr * gr + gi * gi);
-  bool do_rot = valid_me && valid_all[p] && al > tiny && be > tiny && gabs > tiny;
-  float rel = 0.f;
-  if (do_rot) {
-    rel = gabs / sqrtf(al * be);
-    do_rot = rel > tol;
-  }
-  if (do_rot) {
-    if (first) {
-      local_off = fmaxf(local_off, rel);
-      if (lane == 0) ++rot;
-    }
-    const float er = gr / gabs, ei = -gi / gabs;
-    const float zeta = (al - be) / (2.f * gabs);
-    const float sg = zeta >= 0.f ? 1.f : -1.f;
-    const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-    const float c = 1.f / sqrtf(1.f + t * t);
-    const float sn = c * t;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int i = lane + 32 * e;
-      const float2 y = (i < m) ? theirs[i] : float2{0.f, 0.f};
-      const float2 u = first ? x[e] : y;
-      const float2 v = first ? y : x[e];
-      const float2 ve{v.x * er - v.y * ei, v.x * ei + v.y * er};
-      x[e] = first ? float2{c * u.x - sn * ve.x, c * u.y - sn * ve.y}
-                   : float2{sn * u.x + c * ve.x, sn * u.y + c * ve.y};
-    }
-  }
-  __syncthreads();
-}
-
-template <int E>
-__global__ void __launch_bounds__(512, 1) jacobi_wp_kernel(float2* __restrict__ G, int m, int n, int nblk,
-                                                           float tol, int max_sweeps,
-                                                           const double* __restrict__ fro2, float zero_rel,
-                                                           JacobiCtl* ctl) {
-  extern __shared__ float2 sbuf[];          // 16 columns x m
-  __shared__ bool valid_all[16];
-  __shared__ float off_w[16];
-  __shared__ unsigned long long rot_w[16];
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const unsigned nb = gridDim.x;
-  const double fz = (double)zero_rel * (double)zero_rel * (*fro2);
-  const float tiny = (float)fmax(fz, 1e-30);
-  const float conv = fmaxf(tol, 2e-4f);   // stop when a sweep's largest rotation is below conv
-  int sweep = 0;
-  unsigned long long rot = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    float local_off = 0.f;
-    for (int r = 0; r < nblk - 1; ++r) {
-      for (int pb = blockIdx.x; pb < nblk / 2; pb += gridDim.x) {
-        int I, J;
-        round_robin_pair(r, pb, nblk, I, J);
-        const int col = (w < 8 ? I : J) * 8 + (w & 7);
-        const bool valid = col < n;
-        if (lane == 0) valid_all[w] = valid;
-        float2 x[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = lane + 32 * e;
-          x[e] = (valid && i < m) ? G[(long long)col * m + i] : float2{0.f, 0.f};
-        }
-        __syncthreads();
-        if (r == 0) {
-          wp_subround<0, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<1, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<2, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<3, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<4, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<5, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-          wp_subround<6, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        }
-        wp_subround<7, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<8, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<9, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<10, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<11, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<12, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<13, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        wp_subround<14, E>(x, valid, valid_all, sbuf, m, tiny, tol, local_off, rot);
-        if (valid) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int i = lane + 32 * e;
-            if (i < m) G[(long long)col * m + i] = x[e];
-          }
-        }
-        __syncthreads();   // valid_all and sbuf are reused by the next pair of blocks
-      }
-      if (lane == 0) off_w[w] = local_off;
-      __syncthreads();
-      if (tid == 0) {
-        float mx = 0.f;
-        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, off_w[i]);
-        if (mx > 0.f) atomicMax(&ctl->off_bits[sweep & 1], __float_as_uint(mx));
-      }
-      local_off = 0.f;
-      if (!grid_barrier(ctl, nb)) {
-        if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
-        return;
-      }
-      if (r == 0 && blockIdx.x == 0 && tid == 0) ctl->off_bits[(sweep + 1) & 1] = 0u;
-    }
-    const float off = __uint_as_float(*((volatile unsigned*)&ctl->off_bits[sweep & 1]));
-    if (!(off > conv)) { ++sweep; break; }
-  }
-  if (lane == 0 && rot) atomicAdd(&ctl->rotations, rot);
-  (void)rot_w;
-  if (blockIdx.x == 0 && tid == 0) {
-    ctl->sweeps = sweep;
-    const float off = __uint_as_float(ctl->off_bits[(sweep - 1) & 1]);
-    if (sweep >= max_sweeps && off > conv && ctl->err == 0) ctl->err = (int)DMRGC_ENOCONV;
   }
 }
 
@@ -682,16 +363,32 @@ __device__ __forceinline__ void wp4_pair(float2 (&x)[E], const float2 (&y)[E], b
   const float t = -sg / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   const float c = 1.f / sqrtf(1.f + t * t);
   const float sn = c * t;
-  // first: u' = c u - s e^{-i phi} v;  second: v' = s u + c e^{-i phi} v.
-  // With b = (-s or c) e^{-i phi} = (br, bi):  b v = (br vx - bi vy, br vy + bi vx)
-  const float a = FIRST ? c : sn;
-  const float br = (FIRST ? -sn : c) * er, bi = (FIRST ? -sn : c) * ei;
-  const float2 AA{a, a}, BR{br, br}, BI{-bi, bi};
+  // first: u' = c u - s e^{-i phi} v;  second: v' = s u + c e^{-i phi} v,
+  // applied as corrections of the column itself with tau = s / (1 + c), since
+  // c = 1 - s tau:  u' = u + (-s tau u - s e v),  v' = e v + (-s tau e v + s u)
+  // (e = e^{-i phi}).  For small rotations c rounds to 1 while c^2 + s^2 = 1 + t^2
+  // does not; the plain form then grows every column by t^2 / 2 per rotation,
+  // a bias that thousands of late-sweep rotations turn into ~1e-4 of s_1.
+  const float mst = -sn * (sn / (1.f + c));
+  const float2 MST{mst, mst};
+  if (FIRST) {
+    const float br = -sn * er, bi = -sn * ei;
+    const float2 BR{br, br}, BI{-bi, bi};
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const float2 u = FIRST ? x[e] : y[e];
-    const float2 v = FIRST ? y[e] : x[e];
-    x[e] = __ffma2_rn(AA, u, __ffma2_rn(BR, v, __fmul2_rn(BI, make_float2(v.y, v.x))));
+    for (int e = 0; e < E; ++e) {
+      const float2 u = x[e], v = y[e];
+      const float2 d = __ffma2_rn(MST, u, __ffma2_rn(BR, v, __fmul2_rn(BI, make_float2(v.y, v.x))));
+      x[e] = make_float2(u.x + d.x, u.y + d.y);
+    }
+  } else {
+    const float2 ER{er, er}, EI{-ei, ei}, SN{sn, sn};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float2 u = y[e], v = x[e];
+      const float2 ev = __ffma2_rn(ER, v, __fmul2_rn(EI, make_float2(v.y, v.x)));
+      const float2 d = __ffma2_rn(MST, ev, __fmul2_rn(SN, u));
+      x[e] = make_float2(ev.x + d.x, ev.y + d.y);
+    }
   }
 }
 
@@ -1258,7 +955,6 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   int threads = 128, blocks;
   const bool gram = sizeof(R) == 4 && m <= 512 * 2 && n >= 16 && jacobi_variant() == 1;
   const bool wide = !gram && sizeof(R) == 4 && m <= 32 * 32 && n >= 16;
-  const bool blocked = !gram && !wide && sizeof(R) == 4 && m <= 128 * 8 && n >= 16;
   int nblk = 0;
   size_t dyn_smem = 0;
   if (gram) {
@@ -1281,13 +977,6 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
     cudaError_t ea = allow_dyn_smem(fn);
     if (ea != cudaSuccess) return ea;
     blocks = nblk / 2;
-  } else if (blocked) {
-    nblk = (n + 3) / 4;
-    nblk += nblk & 1;
-    if (m <= 128 * 2) fn = (void*)jacobi_blk_kernel<2>;
-    else if (m <= 128 * 4) fn = (void*)jacobi_blk_kernel<4>;
-    else fn = (void*)jacobi_blk_kernel<8>;
-    blocks = nblk / 2;
   } else if (m <= 128 * 16) {
     if (m <= 128 * 2) fn = (void*)jacobi_reg_kernel<R, 2>;
     else if (m <= 128 * 4) fn = (void*)jacobi_reg_kernel<R, 4>;
@@ -1305,7 +994,7 @@ cudaError_t launch_jacobi(void* G, int m, int n, double tol, int max_sweeps, con
   if (blocks < 1) blocks = 1;
   C2* g = reinterpret_cast<C2*>(G);
   R tl = (R)tol, zr = (R)zero_rel;
-  int mm = m, nn = n, npp = (gram || wide || blocked) ? nblk : np, ms = max_sweeps;
+  int mm = m, nn = n, npp = (gram || wide) ? nblk : np, ms = max_sweeps;
   void* args[] = {&g, &mm, &nn, &npp, &tl, &ms, (void*)&fro2, &zr, &c};
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, dyn_smem, st);
 }
@@ -1501,6 +1190,11 @@ extern "C" dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, 
   if (cudaStreamSynchronize(st) != cudaSuccess) return DMRGC_ECUDA;
   *k_out = tr.k;
   return DMRGC_OK;
+}
+
+extern "C" dmrgc_status dmrgc_set_wait_limit(unsigned long long spins) {
+  const unsigned long long v = spins ? spins : dmrgc::kSpinLimitDefault;
+  return cudaMemcpyToSymbol(dmrgc::g_spin_limit, &v, sizeof(v)) == cudaSuccess ? DMRGC_OK : DMRGC_ECUDA;
 }
 
 extern "C" dmrgc_status dmrgc_set_jacobi_kernel(int variant) {

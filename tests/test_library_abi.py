@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     from paper_2207_05612_gb300 import binding
     assert ctypes.sizeof(binding.Gate) == 8 + 32 * 8
-    assert ctypes.sizeof(binding.Stats) == 13 * 8
+    assert ctypes.sizeof(binding.Stats) == 15 * 8
     assert binding.MLP_PARAMS == 21377
     o = binding.dmrgc_default_options()      # host-only entry point
     assert o.precision == binding.DMRGC_FP64 and o.max_jacobi_sweeps == 40
