@@ -11,6 +11,8 @@ Two tiers:
 * `mpo`, `dmrg`: the two-site compression step taken step by step
   (Sec. IV.B, Eq. (scalarproduct), Eq. (optimization), Eq. (Ftilde-sup),
   Eq. (fa-sup)) with numpy einsum and LAPACK SVD.
+* `single_site`: the paper's own single-tensor update with grouped qubits
+  (Sec. IV.A, IV.B.1, V.C), M = F / sqrt(f) from a seeded random guess.
 
 Pins for every function live in tests/test_oracle_*.py.
 """

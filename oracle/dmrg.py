@@ -55,13 +55,19 @@ import numpy as np
 
 
 def make_x(lenv: np.ndarray, b: np.ndarray, w: np.ndarray) -> np.ndarray:
-    """X[a, s, y, c] = sum_{w,b,t} L[a,w,b] B[b,t,c] W[w,s,t,y]."""
-    return np.einsum("awb,btc,wsty->asyc", lenv, b, w, optimize=True)
+    """X[a, s, y, c] = sum_{w,b,t} L[a,w,b] B[b,t,c] W[w,s,t,y], contracted
+    top-down as in Sec. IV.B.2: the environment with the old tensor first,
+    then the layer operator."""
+    lb = np.einsum("awb,btc->awtc", lenv, b, optimize=True)
+    return np.einsum("awtc,wsty->asyc", lb, w, optimize=True)
 
 
 def make_y(renv: np.ndarray, b: np.ndarray, w: np.ndarray) -> np.ndarray:
-    """Y[s, c, y, a] = sum_{w,b,t} R[c,w,b] B[a,t,b] W[y,s,t,w]."""
-    return np.einsum("cwb,atb,ystw->scya", renv, b, w, optimize=True)
+    """Y[s, c, y, a] = sum_{w,b,t} R[c,w,b] B[a,t,b] W[y,s,t,w], contracted
+    bottom-up (Sec. IV.B.2): the environment with the old tensor first, then
+    the layer operator."""
+    rb = np.einsum("cwb,atb->cwat", renv, b, optimize=True)
+    return np.einsum("cwat,ystw->scya", rb, w, optimize=True)
 
 
 def theta_of(x: np.ndarray, y: np.ndarray) -> np.ndarray:

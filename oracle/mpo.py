@@ -33,6 +33,31 @@ def snake_order(rows: int, cols: int) -> list[int]:
     return order
 
 
+def chain_order(rows: int, cols: int, kind: str = "V") -> list[int]:
+    """order[site] = qubit of the chain along which the MPS runs.
+    V: the snake along columns (snake_order); H: the snake along rows (row 0
+    left to right, row 1 right to left, ...); D: the anti-diagonals r + c = d
+    in increasing d, each walked in increasing r for even d, decreasing for
+    odd d.  Groups of consecutive columns, rows or diagonals (Sec. V.C,
+    groupings V, H, D) are then runs of consecutive sites."""
+    if kind == "V":
+        return snake_order(rows, cols)
+    order = []
+    if kind == "H":
+        for r in range(rows):
+            cc = range(cols) if r % 2 == 0 else range(cols - 1, -1, -1)
+            order += [r * cols + c for c in cc]
+        return order
+    if kind == "D":
+        for d in range(rows + cols - 1):
+            rr = list(range(max(0, d - cols + 1), min(rows - 1, d) + 1))
+            if d % 2 == 1:
+                rr.reverse()
+            order += [r * cols + (d - r) for r in rr]
+        return order
+    raise ValueError(kind)
+
+
 def identity_mpo(n: int) -> list[np.ndarray]:
     eye = np.eye(2, dtype=np.complex128).reshape(1, 2, 2, 1)
     return [eye.copy() for _ in range(n)]

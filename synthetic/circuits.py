@@ -190,6 +190,31 @@ def gates_to_records(layer) -> np.ndarray:
     return rec
 
 
+def grouping(rows: int, cols: int, kind: str, widths) -> list[int]:
+    """Qubit groups of the single-site variant (Sec. V.C, groupings V, H, D)
+    on a rows x cols grid: kind "V" groups consecutive columns, "H"
+    consecutive rows, "D" consecutive anti-diagonals r + c = const; widths[g]
+    is the number of such lines in group g (they must add up to all lines).
+    Returns the number of qubits in each group, in the order of the lines.
+    A description of the input only: which qubits share an MPS tensor."""
+    if kind == "V":
+        lines = [rows] * cols
+    elif kind == "H":
+        lines = [cols] * rows
+    elif kind == "D":
+        lines = [min(d + 1, rows, cols, rows + cols - 1 - d) for d in range(rows + cols - 1)]
+    else:
+        raise ValueError(kind)
+    widths = list(widths)
+    if sum(widths) != len(lines) or min(widths) < 1:
+        raise ValueError(f"widths {widths} do not tile the {len(lines)} lines")
+    out, p = [], 0
+    for w in widths:
+        out.append(sum(lines[p:p + w]))
+        p += w
+    return out
+
+
 # Batched workload: independent random-circuit instances of uneven size, depth
 # and bond dimension.  Grid for each qubit count: the nearest near-rectangular one.
 BATCH_GRIDS = {16: (4, 4), 20: (4, 5), 24: (4, 6), 30: (5, 6), 36: (6, 6), 42: (6, 7), 54: (6, 9)}
