@@ -166,11 +166,54 @@ def workload_shapes(rows: int, cols: int, chi: int, layer, compress: bool = True
     return [(chib[i], dmpo[i], chib[i + 1], dmpo[i + 1], chib[i + 2], dmpo[i + 2]) for i in range(n - 1)]
 
 
+def update_flops(shape) -> float:
+    """Complex MACs of one oracle update at a bond (X, Y, theta, environment)."""
+    cl, dl, cm, dm, cr, dr = shape
+    x = cl * dl * cl * 2 * cm + cl * 2 * cm * dl * 2 * dm      # L B, then W
+    y = cr * dr * cr * 2 * cm + cr * 2 * cm * dr * 2 * dm
+    th = 2 * cl * 2 * cr * dm * cm
+    env = cm * 2 * cl * dm * cm
+    return float(x + y + th + env)
+
+
+def stratified_bonds(shapes, count: int):
+    """count bonds of the layer spread evenly over the cost order of one
+    update (the middle of each of count equal-frequency strata), so that their
+    mean time estimates the mean update of the layer."""
+    order = sorted(range(len(shapes)), key=lambda i: update_flops(shapes[i]))
+    return [order[min(len(order) - 1, int((k + 0.5) * len(order) / count))] for k in range(count)]
+
+
+def _oracle_worker(shapes, budget_s, seed, max_updates, q):
+    q.put(oracle_updates(shapes, budget_s, seed, max_updates))
+
+
+def oracle_updates_bounded(shapes, budget_s: float, timeout_s: float, seed: int = 0, max_updates: int = 1 << 30):
+    """oracle_updates in a spawned process that is stopped after timeout_s
+    (one oracle update cannot be interrupted from inside).  Returns the
+    result, or None on timeout."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_worker, args=(shapes, budget_s, seed, max_updates, q))
+    p.start()
+    try:
+        return q.get(timeout=timeout_s)
+    except Exception:
+        return None
+    finally:
+        p.join(5)
+        if p.is_alive():
+            p.kill()
+            p.join(5)
+
+
 def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 << 30):
     """Oracle two-site updates (Sec. IV.B: X, Y, theta, truncated SVD, left
-    environment) on random tensors of the given shapes, bonds drawn uniformly
-    from `shapes` (the cost does not depend on the values), until budget_s of
-    CPU time or max_updates.  Returns (updates, seconds, threads, bonds)."""
+    environment) on random tensors of the given shapes (the cost does not
+    depend on the values), at four bonds spread over the layer's cost order
+    taken in turn, until budget_s of CPU time or max_updates.  Returns
+    (updates, seconds, threads, bonds)."""
     from oracle import dmrg as od
     rng = np.random.default_rng(seed)
 
@@ -178,8 +221,9 @@ def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 
         return rng.normal(size=shape) + 1j * rng.normal(size=shape)
 
     done, spent, picked = 0, 0.0, []
+    strata = stratified_bonds(shapes, 4)
     while done < max_updates and (done == 0 or spent < budget_s):
-        i = int(rng.integers(len(shapes)))
+        i = strata[(done + seed) % len(strata)]
         cl, dl, cm, dm, cr, dr = shapes[i]
         lenv, renv = rnd(cl, dl, cl), rnd(cr, dr, cr)
         b1, b2 = rnd(cl, 2, cm), rnd(cm, 2, cr)
@@ -208,7 +252,7 @@ def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 
 
 
 STAT_KEYS = ("gemm_ms", "gemm_flops", "svd_ms", "svd_flops", "mpo_ms", "other_ms", "kernel_launches",
-             "jacobi_sweeps", "svd_launches", "updates", "eig_svds", "eig_fallbacks")
+             "jacobi_sweeps", "svd_launches", "updates", "eig_svds", "eig_fallbacks", "eig_skipped")
 
 
 def stats_delta(a: dict, b: dict) -> dict:
@@ -253,7 +297,8 @@ def run_ours(args, world, rank, local):
             lf_20 = ctx.fidelity()[0]
         st_w = ctx.stats()
         note(f"warm-up layer {li}: max bond {max(ctx.bond_dims()[0])}, svd {st_w['svd_ms']:.0f} ms, "
-             f"gemm {st_w['gemm_ms']:.0f} ms, eigensolver {st_w['eig_svds']} / fallbacks {st_w['eig_fallbacks']}")
+             f"gemm {st_w['gemm_ms']:.0f} ms, eigensolver {st_w['eig_svds']} / fallbacks {st_w['eig_fallbacks']}"
+             f" / skipped {st_w['eig_skipped']}")
     # the warmed state, for the FP64 comparison on the first timed layer
     warm = None
     if args.fp64_updates > 0 and world == 1 and args.precision != "fp64":
@@ -297,7 +342,8 @@ def run_ours(args, world, rank, local):
         readout = d if readout is None else {key: readout[key] + d[key] for key in STAT_KEYS}
         h2d += len(layer) * 264 + bits.nbytes
         d2h += amps.size * 16 + 16
-        note(f"timed step {k}: svd {s_dev['svd_ms']:.0f} ms, gemm {s_dev['gemm_ms']:.0f} ms (cumulative)")
+        note(f"timed step {k}: svd {s_dev['svd_ms']:.0f} ms, gemm {s_dev['gemm_ms']:.0f} ms, eigensolver "
+             f"{s_dev['eig_svds']} / fallbacks {s_dev['eig_fallbacks']} / skipped {s_dev['eig_skipped']} (cumulative)")
     torch.cuda.synchronize()
     t_region = time.perf_counter() - t_region0
     if world > 1:
@@ -334,8 +380,10 @@ def fp64_comparison(args, warm, layer, hist_mixed, stream, upd_per_step):
     import torch
     from paper_2207_05612_gb300 import Context
     mps, lf_w = warm
+    # the complex64 modes' cutoffs, so that both runs apply the same truncation rules
     ctx = Context(args.rows, args.cols, args.chi, precision=PRECISIONS["fp64"], timing=True,
-                  stream=stream.cuda_stream, mpo_compress=args.mpo_compress)
+                  stream=stream.cuda_stream, mpo_compress=args.mpo_compress,
+                  sweep_rel_cutoff=2e-5, zip_rel_cutoff=4e-3)
     ctx.set_mps(mps, lf_w)
     note("FP64: state loaded")
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -356,9 +404,10 @@ def fp64_comparison(args, warm, layer, hist_mixed, stream, upd_per_step):
             "step_updates_per_s_estimate": upd_per_step / step_s,
             "apply_layer_s": apply_ms / 1e3, "updates_timed": int(args.fp64_updates), "updates_s": upd_ms / 1e3,
             "max_rel_diff_partial_fidelity": float(np.max(np.abs(h64 - hm) / hm)) if len(hm) else None,
-            "sample": f"FP64 context loaded with the warmed state (set_mps), the first timed layer: apply_layer "
-                      f"and the first {args.fp64_updates} updates of its sweep, CUDA events; "
-                      "step estimate = apply_layer + 106 x the mean update time"}
+            "sample": f"FP64 context (complex128, the complex64 modes' cutoffs) loaded with the warmed state "
+                      f"(set_mps), the first timed layer: apply_layer and the first {args.fp64_updates} updates "
+                      "of its sweep, CUDA events; step estimate = apply_layer + 106 x the mean update time; "
+                      "max_rel_diff_partial_fidelity: those updates' f against the timed run's"}
 
 
 def main(argv=None):
@@ -386,7 +435,7 @@ def main(argv=None):
                          "0: the bond is the product of the straddling gates' Schmidt ranks")
     ap.add_argument("--records", type=int, default=20000, help="learned: training records to log")
     ap.add_argument("--eval-layers", type=int, default=4, help="learned: layers of the random circuit to run")
-    ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned"],
+    ap.add_argument("--workload", default="random", choices=["random", "qaoa", "batch", "learned", "grouping"],
                     help="qaoa: grid-graph QAOA (p = --layers), reports the sampled cut value; "
                          "batch: independent instances of uneven N, depth and chi on concurrent streams")
     ap.add_argument("--batch-count", type=int, default=32, help="batch: number of instances")
@@ -407,6 +456,8 @@ def main(argv=None):
         return qaoa_report(args)
     if args.workload == "batch":
         return batch_report(args)
+    if args.workload == "grouping":
+        return grouping_report(args)
     if args.workload == "learned":
         return learned_report(args)
     world, rank, local = dist_setup()
@@ -434,9 +485,9 @@ def main(argv=None):
                 times.append(dt)
         tot = sum(times)
         value = args.steps / tot
-        sample = (f"per step one oracle two-site update at a bond drawn uniformly from the first timed layer's "
-                  f"bonds (the workload's operand shapes: saturated MPS bonds <= {args.chi}, the layer's "
-                  f"compressed MPO bonds; random values)")
+        sample = (f"per step one oracle two-site update, the bonds taken in turn from four cost strata of the "
+                  f"first timed layer's bonds (the workload's operand shapes: saturated MPS bonds <= {args.chi}, "
+                  f"the layer's compressed MPO bonds; random values)")
         line = {"impl": "reference", "metric": "two-site updates/s", "value": value,
                 "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -492,13 +543,19 @@ def main(argv=None):
     if not args.no_cpu_baseline and world == 1:
         note("CPU baseline")
         shapes = workload_shapes(args.rows, args.cols, args.chi, r["first_layer"], compress=bool(args.mpo_compress))
-        done, spent, threads, picked = oracle_updates(shapes, args.cpu_budget, seed=1)
-        note(f"CPU baseline: {done} updates in {spent:.1f} s")
-        cpu = {"value": done / spent, "unit": "updates/s", "cores": threads, "kind": "oracle",
-               "sample": f"{done} oracle two-site updates at bonds drawn uniformly from the timed layer's "
-                         f"{len(shapes)} bonds (operand shapes of the workload: saturated MPS bonds <= {args.chi}, "
-                         f"the layer's compressed MPO bonds; random values), {spent:.1f} s of CPU time, "
-                         f"bonds {sorted(picked)}"}
+        got = oracle_updates_bounded(shapes, args.cpu_budget, 6 * args.cpu_budget + 120, seed=1)
+        if got is None:
+            cpu = {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"no oracle update finished within {6 * args.cpu_budget + 120:.0f} s"}
+            note("CPU baseline timed out")
+        else:
+            done, spent, threads, picked = got
+            note(f"CPU baseline: {done} updates in {spent:.1f} s")
+            cpu = {"value": done / spent, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                   "sample": f"{done} oracle two-site updates at bonds taken in turn from four cost strata "
+                             f"of the timed layer's {len(shapes)} bonds (operand shapes of the workload: saturated "
+                             f"MPS bonds <= {args.chi}, the layer's compressed MPO bonds; random values), "
+                             f"{spent:.1f} s of CPU time, bonds {picked}"}
     line = {
         "metric": "two-site updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps,
@@ -522,6 +579,7 @@ def main(argv=None):
                          "gemm_tflops": st["gemm_flops"] / max(gemm_s, 1e-12) / 1e12,
                          "svd_tflops": st["svd_flops"] / max(svd_s, 1e-12) / 1e12,
                          "eig_svds": st["eig_svds"], "eig_fallbacks": st["eig_fallbacks"],
+                         "eig_skipped": st["eig_skipped"],
                          "jacobi_sweeps": st["jacobi_sweeps"],
                          "note": "device-timed part only (apply_layer + sweeps)"},
         "readout_ms": {"amplitudes_1024": r["readout"]["gemm_ms"] + r["readout"]["other_ms"],
@@ -583,6 +641,75 @@ def fidelity_report(args):
             for name in ("fp64", "fp32", "tf32x3", "bf16x3"):
                 res[name]["rel_err_vs_oracle"] = abs(res[name]["log_F_tilde"] - lo)
         out[f"chi={chi}"] = res
+    print(json.dumps(out))
+    return 0
+
+
+GROUPINGS_4x7 = {   # Sec. V.C on the 4 x 7 grid (the paper's 28-qubit n_b = 4, n_c = 8 size): (kind, widths, K)
+    "V(1^7)": ("V", [1] * 7, 2),          # one column (4 qubits) per tensor
+    "V(2,1,1,1,2)": ("V", [2, 1, 1, 1, 2], 2),
+    "H(1^4)": ("H", [1] * 4, 2),          # one row (7 qubits) per tensor
+    "D(2^5)": ("D", [2] * 5, 1),          # pairs of anti-diagonals; K = 1 as in the paper for D
+}
+
+
+def grouping_report(args):
+    """Error per gate of the random circuits on the 4 x 7 grid for the
+    two-site variant and the single-site variant under several qubit
+    groupings (Sec. V.C, Sec. V.D.2 "role of the qubit grouping"), Sequence I
+    and Sequence II (Sec. V.A): eps = 1 - F~^(1 / N_2g) against chi at the
+    final depth, and against depth at one chi.  BF16x3 (the error per gate
+    needs no more than 1e-4 relative); single-site runs start every step
+    from the seeded random guess and sweep n_s = 4 times, the two-site runs
+    use the zip-up guess and 2 one-direction sweeps.  K = 2 cycles per step,
+    except K = 1 for the diagonal grouping (its two-cycle layer operator has
+    bond 4^7 at some cuts; the paper also runs D with K = 1)."""
+    import math
+    from paper_2207_05612_gb300 import Context
+    from synthetic import circuits as sc
+    rows, cols, cycles = 4, 7, 20
+    chis = (8, 16, 32, 64)
+    chi_depth = 32
+    prec = PRECISIONS["bf16x3"]
+    out = {"report": "grouping", "grid": f"{rows}x{cols}", "cycles": cycles, "precision": "bf16x3",
+           "eps": "1 - F_tilde^(1/N_2g), N_2g the two-qubit gates applied so far", "curves": {}}
+    t_all = time.perf_counter()
+    for seq_name, order in (("I", sc.PATTERN_ORDER), ("II", sc.PATTERN_ORDER_II)):
+        variants = {"two-site": None}
+        variants.update(GROUPINGS_4x7)
+        curves = {}
+        for name, grp in variants.items():
+            k_cyc = 2 if grp is None else grp[2]
+            circ = sc.random_circuit(rows, cols, cycles, cycles_per_layer=k_cyc, seed=args.seed,
+                                     pattern_order=order)
+            n2g = [sum(1 for g in layer if g[1] >= 0) for layer in circ.layers]
+            res = {"K": k_cyc, "eps_vs_chi": {}, "eps_vs_depth": None, "seconds": 0.0}
+            for chi in chis:
+                t0 = time.perf_counter()
+                if grp is None:
+                    ctx = Context(rows, cols, chi, precision=prec)
+                    sweeps = 2
+                else:
+                    kind, widths, _ = grp
+                    ctx = Context(rows, cols, chi, precision=prec, order=kind,
+                                  groups=sc.grouping(rows, cols, kind, widths), seed=args.seed + 17, mpo_compress=1)
+                    sweeps = 4
+                lf_depth, total2 = [], 0
+                for layer, ng in zip(circ.layers, n2g):
+                    ctx.apply_layer(layer)
+                    ctx.sweep(sweeps)
+                    total2 += ng
+                    lf, _ = ctx.fidelity()
+                    lf_depth.append(1.0 - math.exp(lf / total2))
+                ctx.close()
+                res["eps_vs_chi"][chi] = lf_depth[-1]
+                if chi == chi_depth:
+                    res["eps_vs_depth"] = lf_depth
+                res["seconds"] += time.perf_counter() - t0
+            curves[name] = res
+            note(f"grouping: sequence {seq_name} {name}: eps(chi) {res['eps_vs_chi']} ({res['seconds']:.0f} s)")
+        out["curves"][f"sequence {seq_name}"] = curves
+    out["seconds"] = time.perf_counter() - t_all
     print(json.dumps(out))
     return 0
 

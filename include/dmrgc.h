@@ -20,7 +20,8 @@
  *
  * Conventions:
  *  - Qubit q sits at grid position (r, c) with q = r*cols + c.  MPS sites are
- *    ordered as a snake down the columns (down column 0, up column 1, ...).
+ *    ordered along the grid's chain order (dmrgc_grid.order), by default a
+ *    snake down the columns (down column 0, up column 1, ...).
  *  - A gate's matrix is row-major complex128 with re/im interleaved:
  *    <s_q0 s_q1|U|t_q0 t_q1>, q0 the most significant bit (4x4, 32 doubles);
  *    a one-qubit gate (q1 = -1) uses the first 8 doubles as a 2x2 matrix.
@@ -57,7 +58,14 @@ enum {
 
 typedef struct {
   int rows, cols; /* grid shape; n_qubits must equal rows*cols */
-  int order;      /* 0 = snake along columns (the only order) */
+  int order;      /* chain order of the MPS sites: 0 = snake along the columns
+                     (column 0 top to bottom, column 1 bottom to top, ...);
+                     1 = snake along the rows (row 0 left to right, row 1 right
+                     to left, ...); 2 = the anti-diagonals r + c = d in
+                     increasing d, each in increasing r for even d and
+                     decreasing r for odd d.  Runs of consecutive columns, rows
+                     or anti-diagonals are then runs of consecutive sites: the
+                     V, H and D qubit groupings of Sec. V.C. */
 } dmrgc_grid;
 
 typedef struct {
@@ -97,7 +105,7 @@ typedef struct {
                                  0 (default) = the leading eigenvectors of the Gram matrix
                                  G G^+ (TF32x3 product, Householder tridiagonalisation,
                                  bisection and FP64 inverse iteration, back-transformation)
-                                 whenever every kept eigenvalue is at least 1e-4 of the largest
+                                 whenever every kept eigenvalue is at least 1e-5 of the largest
                                  (the Gram's rounding then cannot move the kept subspace), the
                                  Jacobi SVD otherwise; 1 = always the Jacobi SVD.  FP64 mode
                                  always uses the Jacobi SVD. */
@@ -130,6 +138,8 @@ typedef struct {
   long long rsvd_accepted;      /* of which accepted (the rest fell back to Jacobi) */
   long long eig_svds;           /* truncated SVDs done by the Gram eigensolver (svd_path 0) */
   long long eig_fallbacks;      /* Gram eigensolver results not resolved: redone by Jacobi */
+  long long eig_skipped;        /* SVDs sent straight to Jacobi: the last one at that bond was not
+                                   resolvable by the eigensolver */
 } dmrgc_stats;
 
 /* Fill *opt with defaults (FP64, Jacobi, default cutoffs, default stream). */
@@ -140,6 +150,33 @@ dmrgc_status dmrgc_default_options(dmrgc_options* opt);
  * chi: maximum bond dimension (1 .. 4096).  *out receives the context. */
 dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi,
                           const dmrgc_options* opt, dmrgc_ctx** out);
+
+/* The paper's own variant (Sec. IV.A, IV.B.1, V.C): an MPS of n_groups
+ * tensors, tensor tau holding group_sizes[tau] consecutive sites of the chain
+ * order (physical dimension 2^{group_sizes[tau]}, the first site the most
+ * significant bit), optimised one tensor at a time: with the other tensors in
+ * orthogonal form the optimum is M = F / sqrt(f) (Eq. optimization, F the
+ * environment tensor of Eq. scalarproduct).  Each dmrgc_apply_layer starts
+ * from a random tensor train (Sec. V.D.1): bond min(chi, 2^{sites left},
+ * 2^{sites right}, old bond x layer-MPO bond) at each cut, entries
+ * (2u - 1) + i (2u' - 1) with u, u' SplitMix64 uniforms of seed
+ * opt->seed + (layer number - 1) at counters 2e, 2e + 1 for entry e of the
+ * tensors taken in order and row-major; it is brought to orthogonal form with
+ * its centre on tensor 0 by right-to-left factorisations, each remaining
+ * factor carried into the left neighbour.  dmrgc_sweep(ctx, n) then runs n
+ * sweeps, alternately tensors 0..n_groups-1 and back, n_groups updates each;
+ * after an update the tensor is replaced by the isometry spanning the same
+ * space (left or right singular vectors; values at the numerical-zero level
+ * dropped, so a bond can shrink).  1 <= group_sizes[tau] <= 20, summing to
+ * n_qubits; EINVAL otherwise.  Amplitudes, sampling, overlaps and XEB are for
+ * contexts with one qubit per tensor (dmrgc_create) and return EINVAL here;
+ * dmrgc_get_mps returns the grouped tensors. */
+dmrgc_status dmrgc_create_grouped(int n_qubits, const dmrgc_grid* grid, const int* group_sizes, int n_groups,
+                                  int chi, const dmrgc_options* opt, dmrgc_ctx** out);
+
+/* Sites per MPS tensor (*count entries: n_groups for a grouped context, else
+ * n_qubits ones); sizes may be NULL. */
+dmrgc_status dmrgc_group_sizes(const dmrgc_ctx* ctx, int* sizes, int* count);
 
 /* Start one compression step (Sec. IV.B) for the gates of one layer (K
  * cycles, gates in time order).  Builds the layer MPO W_i[D,2,2,D] from the
@@ -203,19 +240,38 @@ dmrgc_status dmrgc_sample(dmrgc_ctx* ctx, long long count, unsigned long long se
 dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count, unsigned long long seed,
                        double* f_b, double* stderr_out);
 
-/* Current bond dimensions of the MPS (n_qubits-1 entries) and of the layer
- * MPO (n_qubits-1 entries); either pointer may be NULL. */
+/* Metropolis sampling of |<x|Psi>|^2 (App. C), for circuits whose
+ * amplitudes are all of one order (Porter-Thomas): `chains` independent
+ * Markov chains over bit strings.  Chain c starts at a uniform random string;
+ * at step t = 1..steps it proposes a uniform random string x' and moves to it
+ * with probability min(|<x'|Psi>|^2 / |<x|Psi>|^2, 1) (always from a string
+ * of weight 0).  The random numbers are SplitMix64 uniforms of `seed` (top 53
+ * bits) at counter g (N + 1) + q for bit q of the string (qubit order; the
+ * bit is 1 iff u >= 1/2) and g (N + 1) + N for the acceptance test, with
+ * g = c (steps + 1) + t (t = 0: the start); x' is taken iff
+ * u |<x|Psi>|^2 < |<x'|Psi>|^2.  Amplitudes as dmrgc_amplitude, all chains
+ * of a step in one batch.  out_bits: host uint8 [chains][steps][n_qubits],
+ * the string of each chain after each step (qubit order); *accepted (may be
+ * NULL): moves made at steps >= 1.  Contexts with one qubit per tensor. */
+dmrgc_status dmrgc_metropolis(dmrgc_ctx* ctx, int chains, int steps, unsigned long long seed,
+                              unsigned char* out_bits, long long* accepted);
+
+/* Current bond dimensions of the MPS (tensors-1 entries: n_qubits-1, or
+ * n_groups-1 for a grouped context) and of the per-site layer MPO
+ * (n_qubits-1 entries); either pointer may be NULL. */
 dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* ctx, int* mps_bonds, int* mpo_bonds);
 
-/* Copy the MPS tensors to the host as complex128: site i has shape
- * [chi_{i-1}][2][chi_i] (row-major), concatenated; *centre receives the
- * orthogonality-centre site.  out must hold dmrgc_mps_size() complex values. */
+/* Copy the MPS tensors to the host as complex128: tensor i has shape
+ * [chi_{i-1}][2^{r_i}][chi_i] (row-major; r_i = 1 unless grouped),
+ * concatenated; *centre receives the orthogonality-centre tensor.  out must
+ * hold dmrgc_mps_size() complex values. */
 long long dmrgc_mps_size(const dmrgc_ctx* ctx);
 dmrgc_status dmrgc_get_mps(const dmrgc_ctx* ctx, double* out_re_im, int* centre);
 
-/* Load an MPS (checkpoint restore): site i has shape [bonds[i]][2][bonds[i+1]]
- * (row-major complex128, concatenated, the layout of dmrgc_get_mps), bonds[0]
- * = bonds[N] = 1 and 1 <= bonds[i] <= chi.  The tensors are converted to the
+/* Load an MPS (checkpoint restore): tensor i has shape
+ * [bonds[i]][2^{r_i}][bonds[i+1]] (row-major complex128, concatenated, the
+ * layout of dmrgc_get_mps; N tensors, or n_groups for a grouped context),
+ * bonds[0] = bonds[N] = 1 and 1 <= bonds[i] <= chi.  The tensors are converted to the
  * context's storage precision and become the state the next
  * dmrgc_apply_layer compresses (|Psi_Q> of Sec. IV.B); log_F_tilde is the
  * running Eq. (Ftilde-sup) sum to continue from.  A state saved with
@@ -265,8 +321,9 @@ dmrgc_status dmrgc_test_svd(int precision, int m, int n, const double* G, int ch
  * of G, Eq. optimization with the bond constraint).  Complex64 precisions
  * only (1..3); 3 <= m <= 2048; 1 <= chi < m.  s_out[m]: the min(chi+1, m)
  * leading singular values, zeros after; U_out[m][k] row-major.  *k_out = k,
- * or -1 when the kept eigenvalues are not all resolved (lambda_{k-1} < 1e-4
- * lambda_0, or the cut rel_cut set k): the sweep then uses the Jacobi SVD. */
+ * or -1 when the kept eigenvalues are not all resolved (lambda_{k-1} < 1e-5
+ * lambda_0, or rel_cut set k while rel_cut^2 < 1e-5): the sweep then uses the
+ * Jacobi SVD. */
 dmrgc_status dmrgc_test_svd_gram(int precision, int m, int n, const double* G, int chi, double rel_cut,
                                  double* s_out, int* k_out, double* U_out);
 

@@ -346,3 +346,32 @@ def sample(a: list[np.ndarray], order: list[int], centre: int, count: int, seed:
             out[j, order[i]] = x
         del v
     return out
+
+
+def metropolis(amp, n: int, chains: int, steps: int, seed: int):
+    """Metropolis sampling of |<x|Psi>|^2 (App. C): chain c starts at a uniform
+    random string x_0 and at step t = 1..steps proposes a uniform random x',
+    accepted with probability min(|<x'|Psi>|^2 / |<x|Psi>|^2, 1) (always when
+    the current weight is 0), else the chain stays.  Random numbers: SplitMix64
+    uniforms of `seed` at counter g (n + 1) + q for bit q (qubit order; the bit
+    is 1 iff u >= 1/2) and g (n + 1) + n for the acceptance test, with
+    g = c (steps + 1) + t; x' is accepted iff u p(x) < p(x').
+    amp(bits [count, n]) -> amplitudes.  Returns (samples [chains, steps, n]
+    uint8, qubit order: the state after each step; accepted proposals)."""
+    out = np.zeros((chains, steps, n), dtype=np.uint8)
+    accepted = 0
+    for c in range(chains):
+        def draw(t):
+            g = c * (steps + 1) + t
+            return np.array([1 if splitmix64_uniform(seed, g * (n + 1) + q) >= 0.5 else 0 for q in range(n)],
+                            dtype=np.uint8), splitmix64_uniform(seed, g * (n + 1) + n)
+        x, _ = draw(0)
+        p = abs(complex(amp(x[None, :])[0])) ** 2
+        for t in range(1, steps + 1):
+            y, u = draw(t)
+            q = abs(complex(amp(y[None, :])[0])) ** 2
+            if p == 0.0 or u * p < q:
+                x, p = y, q
+                accepted += 1
+            out[c, t - 1] = x
+    return out, accepted

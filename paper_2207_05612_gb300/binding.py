@@ -50,7 +50,7 @@ class Stats(C.Structure):
                 ("jacobi_sweeps", C.c_longlong), ("mpo_ms", C.c_double),
                 ("other_ms", C.c_double), ("updates", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("rsvd_attempts", C.c_longlong), ("rsvd_accepted", C.c_longlong),
-                ("eig_svds", C.c_longlong), ("eig_fallbacks", C.c_longlong)]
+                ("eig_svds", C.c_longlong), ("eig_fallbacks", C.c_longlong), ("eig_skipped", C.c_longlong)]
 
 
 class BatchItem(C.Structure):
@@ -75,6 +75,11 @@ def lib():
         P = C.POINTER
         L.dmrgc_default_options.argtypes = [P(Options)]
         L.dmrgc_create.argtypes = [C.c_int, P(Grid), C.c_int, P(Options), P(C.c_void_p)]
+        L.dmrgc_create_grouped.argtypes = [C.c_int, P(Grid), C.c_void_p, C.c_int, C.c_int, P(Options),
+                                           P(C.c_void_p)]
+        L.dmrgc_group_sizes.argtypes = [C.c_void_p, C.c_void_p, P(C.c_int)]
+        L.dmrgc_metropolis.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
+                                       P(C.c_longlong)]
         L.dmrgc_apply_layer.argtypes = [C.c_void_p, P(Gate), C.c_int]
         L.dmrgc_sweep.argtypes = [C.c_void_p, C.c_int, P(C.c_double)]
         L.dmrgc_fidelity.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
@@ -115,7 +120,7 @@ def lib():
         L.dmrgc_mlp_train.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong, fp, fp]
         L.dmrgc_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, P(C.c_float), fp]
         L.dmrgc_mlp_predict.argtypes = [fp, fp, C.c_int, C.c_int, fp]
-        for name in ("dmrgc_set_mps", "dmrgc_sweep_updates", "dmrgc_set_wait_limit", "dmrgc_xeb", "dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
+        for name in ("dmrgc_metropolis", "dmrgc_create_grouped", "dmrgc_group_sizes", "dmrgc_set_mps", "dmrgc_sweep_updates", "dmrgc_set_wait_limit", "dmrgc_xeb", "dmrgc_overlap", "dmrgc_overlap_layer", "dmrgc_set_jacobi_kernel", "dmrgc_set_rank_model", "dmrgc_rank_records", "dmrgc_mlp_train",
                      "dmrgc_mlp_loss_grad", "dmrgc_mlp_predict", "dmrgc_batch_run", "dmrgc_svd_noalloc", "dmrgc_test_gemm", "dmrgc_test_svd", "dmrgc_test_svd_gram", "dmrgc_default_options", "dmrgc_create", "dmrgc_apply_layer", "dmrgc_sweep",
                      "dmrgc_fidelity", "dmrgc_amplitude", "dmrgc_sample", "dmrgc_bond_dims",
                      "dmrgc_get_mps", "dmrgc_step_history", "dmrgc_get_stats", "dmrgc_reset_stats"):
@@ -150,12 +155,31 @@ def dmrgc_default_options() -> Options:
     return o
 
 
-def dmrgc_create(n_qubits: int, rows: int, cols: int, chi: int, options: Options | None = None):
-    g = Grid(rows, cols, 0)
+ORDERS = {"V": 0, "H": 1, "D": 2}   # chain orders: columns, rows, anti-diagonals
+
+
+def dmrgc_create(n_qubits: int, rows: int, cols: int, chi: int, options: Options | None = None,
+                 order: int = 0, groups=None):
+    """groups: None (one qubit per tensor, two-site updates) or the sites per
+    tensor (single-site updates over grouped qubits)."""
+    g = Grid(rows, cols, order)
     h = C.c_void_p()
     opt = options if options is not None else dmrgc_default_options()
-    _check(lib().dmrgc_create(n_qubits, C.byref(g), chi, C.byref(opt), C.byref(h)))
+    if groups is None:
+        _check(lib().dmrgc_create(n_qubits, C.byref(g), chi, C.byref(opt), C.byref(h)))
+    else:
+        gs = np.ascontiguousarray(groups, dtype=np.int32)
+        _check(lib().dmrgc_create_grouped(n_qubits, C.byref(g), gs.ctypes.data, len(gs), chi, C.byref(opt),
+                                          C.byref(h)))
     return h
+
+
+def dmrgc_group_sizes(ctx) -> list[int]:
+    n = C.c_int()
+    _check(lib().dmrgc_group_sizes(ctx, None, C.byref(n)), ctx)
+    out = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(lib().dmrgc_group_sizes(ctx, out.ctypes.data, C.byref(n)), ctx)
+    return out[:n.value].tolist()
 
 
 def dmrgc_apply_layer(ctx, layer) -> None:
@@ -188,6 +212,13 @@ def dmrgc_sample(ctx, count: int, seed: int, n_qubits: int) -> np.ndarray:
     return out
 
 
+def dmrgc_metropolis(ctx, chains: int, steps: int, seed: int, n_qubits: int):
+    out = np.zeros((chains, steps, n_qubits), dtype=np.uint8)
+    acc = C.c_longlong()
+    _check(lib().dmrgc_metropolis(ctx, chains, steps, C.c_ulonglong(seed), out.ctypes.data, C.byref(acc)), ctx)
+    return out, acc.value
+
+
 def dmrgc_bond_dims(ctx, n_qubits: int) -> tuple[list[int], list[int]]:
     a = np.zeros(max(n_qubits - 1, 1), dtype=np.int32)
     b = np.zeros(max(n_qubits - 1, 1), dtype=np.int32)
@@ -200,13 +231,14 @@ def dmrgc_get_mps(ctx, n_qubits: int) -> tuple[list[np.ndarray], int]:
     buf = np.zeros(2 * size, dtype=np.float64)
     centre = C.c_int()
     _check(lib().dmrgc_get_mps(ctx, buf.ctypes.data, C.byref(centre)), ctx)
+    sizes = dmrgc_group_sizes(ctx)
     bonds, _ = dmrgc_bond_dims(ctx, n_qubits)
-    chis = [1] + bonds + [1]
+    chis = [1] + bonds[:len(sizes) - 1] + [1]
     z = buf[0::2] + 1j * buf[1::2]
     out, off = [], 0
-    for i in range(n_qubits):
-        n = chis[i] * 2 * chis[i + 1]
-        out.append(z[off:off + n].reshape(chis[i], 2, chis[i + 1]))
+    for i, r in enumerate(sizes):
+        n = chis[i] * 2 ** r * chis[i + 1]
+        out.append(z[off:off + n].reshape(chis[i], 2 ** r, chis[i + 1]))
         off += n
     return out, centre.value
 
@@ -429,7 +461,7 @@ class Context:
     """Owning handle around the C context (marshalling only)."""
 
     def __init__(self, rows: int, cols: int, chi: int, precision: int = DMRGC_FP64,
-                 timing: bool = False, stream=None, **opts):
+                 timing: bool = False, stream=None, order: str = "V", groups=None, **opts):
         o = dmrgc_default_options()
         o.precision = precision
         o.timing = 1 if timing else 0
@@ -438,7 +470,7 @@ class Context:
         for k, v in opts.items():
             setattr(o, k, v)
         self.n = rows * cols
-        self.h = dmrgc_create(self.n, rows, cols, chi, o)
+        self.h = dmrgc_create(self.n, rows, cols, chi, o, ORDERS[order], groups)
 
     def apply_layer(self, layer):
         dmrgc_apply_layer(self.h, layer)
@@ -454,6 +486,9 @@ class Context:
 
     def sample(self, count: int, seed: int):
         return dmrgc_sample(self.h, count, seed, self.n)
+
+    def metropolis(self, chains: int, steps: int, seed: int):
+        return dmrgc_metropolis(self.h, chains, steps, seed, self.n)
 
     def bond_dims(self):
         return dmrgc_bond_dims(self.h, self.n)

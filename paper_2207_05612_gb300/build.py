@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libdmrgc.so")
-SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "svd_jacobi.cu", "mpo_build.cu", "misc.cu", "readout.cu", "mlp.cu", "eig_herm.cu"]
+SOURCES = ["api.cu", "gemm_simt.cu", "gemm_tc.cu", "svd_jacobi.cu", "mpo_build.cu", "misc.cu", "readout.cu", "mlp.cu", "eig_herm.cu", "single_site.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

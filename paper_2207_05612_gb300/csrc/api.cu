@@ -21,88 +21,20 @@
 #include <thread>
 #include <vector>
 
-#include "common.cuh"
+#include "ctx.cuh"
 
 using namespace dmrgc;
 
-namespace {
+using namespace dmrgc_host;
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-};
 
-struct EnvRef {
-  const void* p = nullptr;
-  int a = 1, w = 1, b = 1;   // [a][w][b]
-};
-
-enum TimeClass { TC_GEMM = 0, TC_SVD = 1, TC_MPO = 2, TC_OTHER = 3 };
-
-}  // namespace
-
-struct dmrgc_ctx {
-  int N = 0, chi = 0, rows = 0, cols = 0, m = 0;
-  dmrgc_options opt{};
-  cudaStream_t st = nullptr;
-  bool fp64 = true;
-  size_t esz = 16;
-  double sweep_cut = 1e-12, zip_cut = 1e-5, zero_rel = 1e-13, tie_rel = 1e-10;
-  int max_jsweeps = 40;
-  std::vector<int> order, site_of;
-  std::vector<DevBuf> A, B, Wx, Wy, XY, E;
-  std::vector<DevBuf> Wc;   // layer MPO in [w_in][s][t][w_out] while it is compressed
-  std::vector<int> chiA, chiB, D;     // N+1 entries each
-  std::vector<char> xyk;
-  DevBuf envL, envR, T, theta, jw, bt, one, jctl, tres, scal, gates_d, rank_d, fa_d, fb_d, plan_d;
-  DevBuf ptrs_d, bonds_d, order_d, bits_d, out_d, stage_d, tcerr;
-  DevBuf ovl[2];   // ping-pong environments of dmrgc_overlap (never the sweep's envL / envR)
-  DevBuf ework;    // work space of the Gram eigensolver path (eig_truncate)
-  DevBuf rv[3];    // read-outs: running rows V, site products W = V A_i, T = W E_i
-  TcWork tcw;
-  // randomized SVD and the rank model (svd_mode 1, 2)
-  DevBuf rs_om, rs_y, rs_q, rs_b, rs_h, rs_w, feat, mlp_w, mlp_out, lab;
-  int layer_no = 0;
-  std::vector<int> visit_layer;   // per bond: layer of the last update there (-1 none)
-  std::vector<int> kprev;         // per bond: kept rank at the last update (0 = none)
-  unsigned long long rs_ctr = 0;  // counter of the sketch random stream
-  double rs_tol = 1e-6;
-  int rs_p = 8, rs_pow = 1;
-  bool mlp_ready = false;
-  std::vector<float> rec_x, rec_y;   // logged (features, label) records
-  EnvRef L, R;
-  int phase = 0;           // 0 created, 1 guess ready / sweeping
-  int bond = 0, dir = -1;  // next update (bond, bond+1), dir -1 = right-to-left
-  int centre = 0;
-  double log_ft = 0.0, f_cur = 1.0;
-  std::vector<double> hist;
-  std::string err;
-  dmrgc_stats stats{};
-  struct Pend { int cls; cudaEvent_t a, b; double flops; };
-  std::vector<Pend> pend;
-  std::vector<cudaEvent_t> pool;
-  ~dmrgc_ctx();
-};
-
-namespace {
+namespace dmrgc_host {
 
 dmrgc_status fail(dmrgc_ctx* c, dmrgc_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
 }
 
-#define CK(x)                                                                          \
-  do {                                                                                 \
-    cudaError_t e_ = (x);                                                              \
-    if (e_ != cudaSuccess)                                                             \
-      return fail(c, DMRGC_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));    \
-  } while (0)
-
-#define TRY(x)                          \
-  do {                                  \
-    dmrgc_status s_ = (x);              \
-    if (s_ != DMRGC_OK) return s_;      \
-  } while (0)
 
 dmrgc_status ensure(dmrgc_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -142,25 +74,6 @@ cudaEvent_t take_event(dmrgc_ctx* c) {
   return e;
 }
 
-struct Span {
-  dmrgc_ctx* c;
-  int cls;
-  double flops;
-  cudaEvent_t a = nullptr;
-  Span(dmrgc_ctx* c_, int cls_, double flops_ = 0) : c(c_), cls(cls_), flops(flops_) {
-    if (c->opt.timing) {
-      a = take_event(c);
-      cudaEventRecord(a, c->st);
-    }
-  }
-  ~Span() {
-    if (c->opt.timing) {
-      cudaEvent_t b = take_event(c);
-      cudaEventRecord(b, c->st);
-      c->pend.push_back({cls, a, b, flops});
-    }
-  }
-};
 
 void flush_timing(dmrgc_ctx* c) {
   for (auto& p : c->pend) {
@@ -198,7 +111,7 @@ cudaError_t run_gemm(int precision, const GemmArgs& g, TcWork* w, int* err_dev, 
   return gemm_simt(g, precision == DMRGC_FP64, st);
 }
 
-dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g, int precision = -1) {
+dmrgc_status gemm(dmrgc_ctx* c, const GemmArgs& g, int precision) {
   if (precision < 0) precision = c->opt.precision;
   const bool tc = precision == DMRGC_BF16X3 || precision == DMRGC_TF32X3;
   if (tc && !c->tcerr.p) {
@@ -275,13 +188,12 @@ double jacobi_tol(const dmrgc_ctx* c, int m) {
 // W: the matrix (default jw); chi_cap: the most columns kept (default chi);
 // norm2 (optional): the sum of all s^2.
 dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool squared, double tie_rel,
-                         int& k, double& f, int* nnz = nullptr, double* norm2 = nullptr,
-                         void* W = nullptr, int chi_cap = -1) {
+                         int& k, double& f, int* nnz, double* norm2, void* W, int chi_cap) {
   if (!W) W = c->jw.p;
   if (chi_cap < 0) chi_cap = c->chi;
   TRY(ensure(c, c->jctl, jacobi_ctl_bytes(n)));
   TRY(ensure(c, c->tres, trunc_bytes(n)));
-  TRY(ensure(c, c->scal, 64));
+  TRY(ensure(c, c->scal, 64 + 256 * sizeof(double)));
   double* fro2 = (double*)c->scal.p + 1;
   {
     Span sp(c, TC_SVD);
@@ -304,6 +216,7 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
     return fail(c, DMRGC_ENOCONV, "Jacobi SVD did not converge in " + std::to_string(c->max_jsweeps) + " sweeps");
   if (tr.status != 0 || !std::isfinite(tr.f) || !(tr.f > 0))
     return fail(c, DMRGC_ENUMERIC, "truncated SVD met a zero or non-finite spectrum");
+  c->last_tr = tr;
   c->stats.jacobi_sweeps += ctl.sweeps;
   c->stats.svd_flops += (double)ctl.sweeps * 0.5 * n * (n - 1) * 16.0 * m + (double)ctl.rotations * 14.0 * m;
   k = tr.k;
@@ -323,17 +236,34 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
 // all resolved above the Gram's rounding level (or the path does not apply):
 // the caller then runs the Jacobi SVD.  out receives the k vectors in layout
 // `mode` (see eig_truncate).
-constexpr double kEigResolve = 1e-4;   // lambda_{k-1} >= 1e-4 lambda_0, i.e. s_{k-1} >= 1e-2 s_1
+// lambda_{k-1} >= 1e-5 lambda_0 (s_{k-1} >= 3e-3 s_1): ten times the Gram
+// path's absolute eigenvalue error (~1e-6 lambda_0 for a TF32x3 Gram and an
+// FP32 reduction), so only directions whose weights differ by less than that
+// can trade places at the cut
+constexpr double kEigResolve = 1e-5;
 constexpr int kEigMinN = 128;
 
 bool eig_applies(const dmrgc_ctx* c, int rows) {
   return !c->fp64 && c->opt.svd_path == 0 && rows >= kEigMinN && rows <= 2048 && c->chi < rows;
 }
 
-dmrgc_status eig_try(dmrgc_ctx* c, const void* G, int rows, int kdim, bool conj_cols, double cut, double tie,
-                     DevBuf& out, int mode, int& k, bool& done) {
+// after a truncated SVD at `bond` (either path): would the eigensolver have
+// resolved it?  Spectra change little between visits of a bond, so the next
+// visit tries the eigensolver only if this one was resolvable, and otherwise
+// goes straight to the Jacobi SVD instead of paying for a declined attempt.
+void note_resolvable(dmrgc_ctx* c, int bond) {
+  if (bond < 0 || bond >= (int)c->eig_ok.size()) return;
+  c->eig_ok[bond] = (!c->last_tr.by_cut && c->last_tr.tail >= kEigResolve) ? 1 : 0;
+}
+
+dmrgc_status eig_try(dmrgc_ctx* c, int bond, const void* G, int rows, int kdim, bool conj_cols, double cut,
+                     double tie, DevBuf& out, int mode, int& k, bool& done) {
   done = false;
   if (!eig_applies(c, rows)) return DMRGC_OK;
+  if (bond >= 0 && bond < (int)c->eig_ok.size() && !c->eig_ok[bond]) {
+    c->stats.eig_skipped++;
+    return DMRGC_OK;
+  }
   TRY(ensure(c, c->jw, (size_t)rows * rows * c->esz));
   GemmArgs g;   // H[r1][r2] = sum_x G[r1][x] conj(G[r2][x])
   g.M = rows; g.N = rows; g.K = kdim;
@@ -354,14 +284,21 @@ dmrgc_status eig_try(dmrgc_ctx* c, const void* G, int rows, int kdim, bool conj_
   {
     Span sp(c, TC_SVD);
     int launches = 0;
-    CK(eig_truncate(c->jw.p, rows, c->chi, cut, tie, kEigResolve, c->ework.p, c->tres.p, out.p, mode, c->st,
-                    &launches));
+    const cudaError_t ee = eig_truncate(c->jw.p, rows, c->chi, cut, tie, kEigResolve, c->ework.p, c->tres.p,
+                                       out.p, mode, c->st, &launches);
+    if (ee == cudaErrorInvalidConfiguration || ee == cudaErrorInvalidValue) {
+      cudaGetLastError();   // a size or launch shape the eigensolver does not take: Jacobi SVD
+      c->stats.eig_fallbacks++;
+      return DMRGC_OK;
+    }
+    CK(ee);
     c->stats.svd_launches += launches;
     c->stats.kernel_launches += launches;
   }
   TruncResult tr{};
   CK(cudaMemcpyAsync(&tr, c->tres.p, sizeof(tr), cudaMemcpyDeviceToHost, c->st));
   TRY(sync(c));
+  c->last_tr = tr;
   if (tr.status == DMRGC_ETIMEOUT) return fail(c, DMRGC_ETIMEOUT, "Gram eigensolver grid barrier timed out");
   if (tr.status == DMRGC_ENUMERIC) return fail(c, DMRGC_ENUMERIC, "Gram eigensolver met a zero or non-finite spectrum");
   if (tr.status != 0) {   // 1: not resolved, 2: a non-finite value: the Jacobi SVD decides
@@ -377,11 +314,11 @@ dmrgc_status eig_try(dmrgc_ctx* c, const void* G, int rows, int kdim, bool conj_
 
 // f = |A|^2 of the unnormalised block just formed, then A /= sqrt(f)
 dmrgc_status normalise_block(dmrgc_ctx* c, void* A, long long elems, double& f) {
-  TRY(ensure(c, c->scal, 64));
+  TRY(ensure(c, c->scal, 64 + 256 * sizeof(double)));
   {
     Span sp(c, TC_OTHER);
-    CK(norm2_scale(A, elems, (double*)c->scal.p, true, c->st));
-    c->stats.kernel_launches++;
+    CK(norm2_scale(A, elems, c->fp64, (double*)c->scal.p, (double*)c->scal.p + 8, true, c->st));
+    c->stats.kernel_launches += 2;
   }
   CK(cudaMemcpyAsync(&f, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   TRY(sync(c));
@@ -452,7 +389,7 @@ dmrgc_status rsvd_try(dmrgc_ctx* c, int i, bool adj, int mrow, int ncol, int l, 
   const int opGT = adj ? OP_R : OP_T;
   const int opGc = adj ? OP_T : OP_R;
   const int opG = adj ? OP_C : OP_N;
-  TRY(ensure(c, c->scal, 64));
+  TRY(ensure(c, c->scal, 64 + 256 * sizeof(double)));
   double* fro_t = (double*)c->scal.p + 3;
   TRY(ensure(c, c->rs_om, (size_t)ng * l * es));
   TRY(ensure(c, c->rs_y, (size_t)l * std::max(mg, ng) * es));
@@ -650,7 +587,7 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
     TRY(record_end(c, i, k, false, rec));
   } else {
     // U_k: leading eigenvectors of theta theta^+ where they are resolved, else Jacobi
-    TRY(eig_try(c, c->theta.p, mrow, ncol, false, c->sweep_cut, 0.0, c->A[i], 0, k, eig));
+    TRY(eig_try(c, i, c->theta.p, mrow, ncol, false, c->sweep_cut, 0.0, c->A[i], 0, k, eig));
     if (!eig) {
       TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
       {
@@ -664,6 +601,7 @@ dmrgc_status update_ltr(dmrgc_ctx* c, int i) {
       CK(gather_columns(c->jw.p, mrow, ncol, k, c->tres.p, false, 0, c->A[i].p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
+    note_resolvable(c, i);
     TRY(record_end(c, i, k, true, rec));
   }
   TRY(ensure(c, c->A[i + 1], (size_t)k * ncol * c->esz));
@@ -717,7 +655,7 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
     TRY(record_end(c, i, k, false, rec));
   } else {
     // V_k^+: leading eigenvectors of theta^+ theta (conjugated rows) where resolved, else Jacobi
-    TRY(eig_try(c, c->theta.p, ncol, mrow, true, c->sweep_cut, 0.0, c->A[i + 1], 2, k, eig));
+    TRY(eig_try(c, i, c->theta.p, ncol, mrow, true, c->sweep_cut, 0.0, c->A[i + 1], 2, k, eig));
     if (!eig) {
       TRY(ensure(c, c->jw, (size_t)mrow * ncol * c->esz));
       {
@@ -732,6 +670,7 @@ dmrgc_status update_rtl(dmrgc_ctx* c, int i) {
       CK(gather_columns(c->jw.p, ncol, mrow, k, c->tres.p, false, 2, c->A[i + 1].p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
+    note_resolvable(c, i);
     TRY(record_end(c, i, k, true, rec));
   }
   TRY(ensure(c, c->A[i], (size_t)mrow * k * c->esz));
@@ -801,7 +740,7 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
     int k;
     double f;
     bool eig = false;
-    TRY(eig_try(c, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 0, k, eig));
+    TRY(eig_try(c, i, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 0, k, eig));
     if (!eig) {
       TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
       TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
@@ -837,7 +776,7 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
     int k;
     double f;
     bool eig = false;
-    TRY(eig_try(c, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 1, k, eig));
+    TRY(eig_try(c, i - 1, c->XY[i].p, r, kdim, false, c->zip_cut, c->tie_rel, c->A[i], 1, k, eig));
     if (!eig) {
       TRY(gram_colmajor(c, c->XY[i].p, r, kdim));
       TRY(svd_columns(c, r, r, c->zip_cut, true, c->tie_rel, k, f));
@@ -868,7 +807,7 @@ dmrgc_status zip_guess(dmrgc_ctx* c) {
   g.B = R.p; g.ldb = kdim; g.opB = OP_T;
   g.C = c->A[m].p; g.ldc = ncol;
   TRY(gemm(c, g));
-  TRY(ensure(c, c->scal, 64));
+  TRY(ensure(c, c->scal, 64 + 256 * sizeof(double)));
   {
     Span sp(c, TC_OTHER);
     CK(sum_abs2(c->A[m].p, (long long)mrow * ncol, c->fp64, (double*)c->scal.p, c->st));
@@ -1123,15 +1062,15 @@ dmrgc_status run_updates(dmrgc_ctx* c, long long total) {
   return sync(c);
 }
 
-}  // namespace
+}  // namespace dmrgc_host
 
 dmrgc_ctx::~dmrgc_ctx() {
   auto fr = [](DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; };
-  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &Wc})
+  for (auto* v : {&A, &B, &Wx, &Wy, &XY, &E, &Wc, &GL, &GR})
     for (auto& b : *v) fr(b);
   for (DevBuf* b : {&envL, &envR, &T, &theta, &jw, &bt, &one, &jctl, &tres, &scal, &gates_d, &rank_d,
                     &fa_d, &fb_d, &plan_d, &ptrs_d, &bonds_d, &order_d, &bits_d, &out_d, &stage_d, &tcerr,
-                    &ovl[0], &ovl[1], &ework, &rv[0], &rv[1], &rv[2]})
+                    &ovl[0], &ovl[1], &ework, &rv[0], &rv[1], &rv[2], &gx[0], &gx[1], &gf})
     fr(*b);
   tcw.release();
   for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -1159,7 +1098,7 @@ namespace {
 
 bool valid_shape(int n_qubits, const dmrgc_grid* grid, int chi) {
   return grid && n_qubits >= 1 && n_qubits <= 4096 && grid->rows >= 1 && grid->cols >= 1 &&
-         grid->rows * grid->cols == n_qubits && grid->order == 0 && chi >= 1 && chi <= 4096;
+         grid->rows * grid->cols == n_qubits && grid->order >= 0 && grid->order <= 2 && chi >= 1 && chi <= 4096;
 }
 
 // (Re)initialise a context for a new circuit in |0...0>.  Device buffers the
@@ -1186,11 +1125,27 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
   c->zip_cut = c->opt.zip_rel_cutoff > 0 ? c->opt.zip_rel_cutoff : (c->fp64 ? 1e-5 : 4e-3);
   c->max_jsweeps = c->opt.max_jacobi_sweeps > 0 ? c->opt.max_jacobi_sweeps : 40;
   c->order.clear();
-  for (int col = 0; col < c->cols; ++col)
-    for (int k = 0; k < c->rows; ++k) {
-      const int r = (col % 2 == 0) ? k : c->rows - 1 - k;
-      c->order.push_back(r * c->cols + col);
+  if (grid->order == 0) {          // snake along the columns
+    for (int col = 0; col < c->cols; ++col)
+      for (int k = 0; k < c->rows; ++k) {
+        const int r = (col % 2 == 0) ? k : c->rows - 1 - k;
+        c->order.push_back(r * c->cols + col);
+      }
+  } else if (grid->order == 1) {   // snake along the rows
+    for (int r = 0; r < c->rows; ++r)
+      for (int k = 0; k < c->cols; ++k) {
+        const int col = (r % 2 == 0) ? k : c->cols - 1 - k;
+        c->order.push_back(r * c->cols + col);
+      }
+  } else {                         // anti-diagonals r + col = d, alternating direction
+    for (int d = 0; d < c->rows + c->cols - 1; ++d) {
+      const int r0 = std::max(0, d - c->cols + 1), r1 = std::min(c->rows - 1, d);
+      for (int k = 0; k <= r1 - r0; ++k) {
+        const int r = (d % 2 == 0) ? r0 + k : r1 - k;
+        c->order.push_back(r * c->cols + (d - r));
+      }
     }
+  }
   c->site_of.assign(n_qubits, 0);
   for (int i = 0; i < n_qubits; ++i) c->site_of[c->order[i]] = i;
   for (auto* v : {&c->A, &c->B, &c->Wx, &c->Wy, &c->XY, &c->E, &c->Wc})
@@ -1201,11 +1156,17 @@ dmrgc_status ctx_setup(dmrgc_ctx* c, int n_qubits, const dmrgc_grid* grid, int c
   c->layer_no = 0;
   c->visit_layer.assign(n_qubits, -1);
   c->kprev.assign(n_qubits, 0);
+  c->eig_ok.assign(n_qubits, 1);
   c->rs_ctr = 0;
   c->rs_p = c->opt.rsvd_oversample > 0 ? c->opt.rsvd_oversample : 8;
   c->rs_pow = c->opt.rsvd_power_iters >= 0 ? c->opt.rsvd_power_iters : 1;
   c->rs_tol = c->opt.rsvd_tolerance > 0 ? c->opt.rsvd_tolerance : (c->fp64 ? 1e-6 : 2e-5);
   c->rec_x.clear(); c->rec_y.clear();
+  c->ng = 0;
+  c->gsize.assign(n_qubits, 1);
+  c->gstart.resize(n_qubits);
+  for (int i = 0; i < n_qubits; ++i) c->gstart[i] = i;
+  c->gsweep = 0;
   c->phase = 0; c->bond = 0; c->dir = -1; c->centre = 0;
   c->log_ft = 0.0; c->f_cur = 1.0;
   c->hist.clear();
@@ -1238,6 +1199,48 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi, const d
   dmrgc_status s = ctx_setup(c, n_qubits, grid, chi, o);
   if (s != DMRGC_OK) { delete c; return s; }
   *out = c;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_create_grouped(int n_qubits, const dmrgc_grid* grid, const int* group_sizes, int n_groups,
+                                  int chi, const dmrgc_options* opt, dmrgc_ctx** out) {
+  if (!out || !grid || !group_sizes || n_groups < 1 || n_groups > n_qubits) return DMRGC_EINVAL;
+  *out = nullptr;
+  if (!valid_shape(n_qubits, grid, chi)) return DMRGC_EINVAL;
+  int total = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    if (group_sizes[g] < 1 || group_sizes[g] > 20) return DMRGC_EINVAL;
+    total += group_sizes[g];
+  }
+  if (total != n_qubits) return DMRGC_EINVAL;
+  dmrgc_ctx* c = nullptr;
+  dmrgc_status s = dmrgc_create(n_qubits, grid, chi, opt, &c);
+  if (s != DMRGC_OK) return s;
+  c->ng = n_groups;
+  c->gsize.assign(group_sizes, group_sizes + n_groups);
+  c->gstart.assign(n_groups, 0);
+  for (int g = 1; g < n_groups; ++g) c->gstart[g] = c->gstart[g - 1] + c->gsize[g - 1];
+  c->chiA.assign(n_groups + 1, 1);
+  c->chiB.assign(n_groups + 1, 1);
+  for (int g = 0; g < n_groups; ++g) {   // |0...0>: entry s = 0 of each [1][2^r][1] tensor
+    const size_t n = (size_t)1 << c->gsize[g];
+    s = ensure(c, c->B[g], n * c->esz);
+    if (s == DMRGC_OK && cudaMemsetAsync(c->B[g].p, 0, n * c->esz, c->st) != cudaSuccess) s = DMRGC_ECUDA;
+    if (s == DMRGC_OK && set_scalar_one(c->B[g].p, c->fp64, c->st) != cudaSuccess) s = DMRGC_ECUDA;
+    if (s != DMRGC_OK) { dmrgc_destroy(c); return s; }
+  }
+  s = sync(c);
+  if (s != DMRGC_OK) { dmrgc_destroy(c); return s; }
+  *out = c;
+  return DMRGC_OK;
+}
+
+dmrgc_status dmrgc_group_sizes(const dmrgc_ctx* c, int* sizes, int* count) {
+  if (!c) return DMRGC_EINVAL;
+  const int nt = c->ng > 0 ? c->ng : c->N;
+  if (sizes)
+    for (int g = 0; g < nt; ++g) sizes[g] = c->gsize[g];
+  if (count) *count = nt;
   return DMRGC_OK;
 }
 
@@ -1366,6 +1369,11 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
   c->hist.clear();
   c->layer_no++;
   TRY(build_mpo(c, gates, n_gates));
+  if (c->ng > 0) {   // single-site variant: random guess in orthogonal form
+    TRY(grouped_guess(c));
+    c->phase = 1;
+    return DMRGC_OK;
+  }
   std::fill(c->xyk.begin(), c->xyk.end(), 0);
   TRY(zip_guess(c));
   c->bond = c->m - 1;
@@ -1378,7 +1386,8 @@ dmrgc_status dmrgc_sweep(dmrgc_ctx* c, int n_sweeps, double* f_last) {
   if (!c) return DMRGC_EINVAL;
   if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep before dmrgc_apply_layer");
   if (n_sweeps < 0) return fail(c, DMRGC_EINVAL, "n_sweeps < 0");
-  TRY(run_updates(c, (long long)n_sweeps * (c->N - 1)));
+  if (c->ng > 0) TRY(grouped_sweeps(c, n_sweeps));
+  else TRY(run_updates(c, (long long)n_sweeps * (c->N - 1)));
   if (f_last) *f_last = c->f_cur;
   return DMRGC_OK;
 }
@@ -1422,13 +1431,13 @@ dmrgc_status readout_site(dmrgc_ctx* c, const void* Ai, int B, int l, int r) {
   return gemm(c, g, readout_precision(c));
 }
 
-dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
-  if (!c) return DMRGC_EINVAL;
-  if (count < 0 || (count > 0 && (!bits || !out_re_im))) return fail(c, DMRGC_EINVAL, "bad amplitude arguments");
-  if (count == 0) return DMRGC_OK;
-  if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
-  for (long long j = 0; j < count * c->N; ++j)
-    if (bits[j] > 1) return fail(c, DMRGC_EINVAL, "bits must be 0 or 1");
+}  // extern "C"
+
+namespace dmrgc_host {
+
+// <x|Psi> for count strings already on the device (bits_dev [count][N], qubit
+// order) into out_dev[count] (complex128), chunk by chunk
+dmrgc_status amplitudes_device(dmrgc_ctx* c, const unsigned char* bits_dev, long long count, double2* out_dev) {
   std::vector<int>* bonds;
   auto& st = current_state(c, bonds);
   const int N = c->N;
@@ -1436,12 +1445,9 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
   const int B0 = readout_chunk(c, count, maxb);
   TRY(ensure(c, c->rv[0], (size_t)B0 * maxb * c->esz));
   TRY(ensure(c, c->rv[1], (size_t)B0 * 2 * maxb * c->esz));
-  TRY(ensure(c, c->bits_d, (size_t)count * N));
-  TRY(ensure(c, c->out_d, (size_t)count * sizeof(double2)));
-  CK(cudaMemcpyAsync(c->bits_d.p, bits, (size_t)count * N, cudaMemcpyHostToDevice, c->st));
   for (long long row0 = 0; row0 < count; row0 += B0) {
     const int B = (int)std::min<long long>(B0, count - row0);
-    const unsigned char* bd = (const unsigned char*)c->bits_d.p + row0 * N;
+    const unsigned char* bd = bits_dev + row0 * N;
     {
       Span sp(c, TC_OTHER);
       CK(readout_start(c->rv[0].p, B, c->fp64, c->st));
@@ -1455,18 +1461,80 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
       c->stats.kernel_launches++;
     }
     Span sp(c, TC_OTHER);
-    CK(amp_store(c->rv[0].p, B, (double2*)c->out_d.p + row0, c->fp64, c->st));
+    CK(amp_store(c->rv[0].p, B, out_dev + row0, c->fp64, c->st));
     c->stats.kernel_launches++;
   }
+  return DMRGC_OK;
+}
+
+}  // namespace dmrgc_host
+
+extern "C" {
+
+dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
+  if (!c) return DMRGC_EINVAL;
+  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "amplitude: contexts with one qubit per tensor only");
+  if (count < 0 || (count > 0 && (!bits || !out_re_im))) return fail(c, DMRGC_EINVAL, "bad amplitude arguments");
+  if (count == 0) return DMRGC_OK;
+  if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
+  for (long long j = 0; j < count * c->N; ++j)
+    if (bits[j] > 1) return fail(c, DMRGC_EINVAL, "bits must be 0 or 1");
+  const int N = c->N;
+  TRY(ensure(c, c->bits_d, (size_t)count * N));
+  TRY(ensure(c, c->out_d, (size_t)count * sizeof(double2)));
+  CK(cudaMemcpyAsync(c->bits_d.p, bits, (size_t)count * N, cudaMemcpyHostToDevice, c->st));
+  TRY(amplitudes_device(c, (const unsigned char*)c->bits_d.p, count, (double2*)c->out_d.p));
   CK(cudaMemcpyAsync(out_re_im, c->out_d.p, (size_t)count * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
   return sync(c);
+}
+
+dmrgc_status dmrgc_metropolis(dmrgc_ctx* c, int chains, int steps, unsigned long long seed, unsigned char* out_bits,
+                              long long* accepted) {
+  if (!c) return DMRGC_EINVAL;
+  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "metropolis: contexts with one qubit per tensor only");
+  if (chains < 1 || steps < 1 || !out_bits || (long long)chains * (steps + 1) > (1ll << 40))
+    return fail(c, DMRGC_EINVAL, "bad metropolis arguments");
+  const int N = c->N;
+  const size_t outb = (size_t)chains * steps * N;
+  TRY(ensure(c, c->bits_d, (size_t)chains * N * 2));   // proposals, current strings
+  TRY(ensure(c, c->out_d, (size_t)chains * (sizeof(double2) + 2 * sizeof(double) + sizeof(long long))));
+  TRY(ensure(c, c->stage_d, outb));
+  unsigned char* prop = (unsigned char*)c->bits_d.p;
+  unsigned char* cur = prop + (size_t)chains * N;
+  double2* amp = (double2*)c->out_d.p;
+  double* uacc = (double*)(amp + chains);
+  double* pcur = uacc + chains;
+  long long* acc = (long long*)(pcur + chains);
+  CK(cudaMemsetAsync(acc, 0, (size_t)chains * sizeof(long long), c->st));
+  for (int t = 0; t <= steps; ++t) {
+    {
+      Span sp(c, TC_OTHER);
+      CK(metro_draw(prop, uacc, chains, N, steps, t, seed, c->st));
+      c->stats.kernel_launches++;
+    }
+    TRY(amplitudes_device(c, prop, chains, amp));
+    Span sp(c, TC_OTHER);
+    CK(metro_step(prop, amp, uacc, cur, pcur, acc, (unsigned char*)c->stage_d.p, chains, N, steps, t, c->st));
+    c->stats.kernel_launches++;
+  }
+  CK(cudaMemcpyAsync(out_bits, c->stage_d.p, outb, cudaMemcpyDeviceToHost, c->st));
+  std::vector<long long> a(chains);
+  CK(cudaMemcpyAsync(a.data(), acc, (size_t)chains * sizeof(long long), cudaMemcpyDeviceToHost, c->st));
+  TRY(sync(c));
+  if (accepted) {
+    long long tot = 0;
+    for (long long v : a) tot += v;
+    *accepted = tot;
+  }
+  return DMRGC_OK;
 }
 
 dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
   if (!a || !b || !out_re_im) return DMRGC_EINVAL;
   dmrgc_ctx* c = a;   // errors are reported on a
-  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64)
-    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid and storage precision");
+  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64 || a->order != b->order)
+    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid, order and storage precision");
+  if (a->ng > 0 || b->ng > 0) return fail(a, DMRGC_EINVAL, "overlap: contexts with one qubit per tensor only");
   std::vector<int>* ba;
   std::vector<int>* bb;
   auto& sa = current_state(a, ba);
@@ -1512,8 +1580,9 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
                                  double* out_re_im) {
   if (!a || !b || !out_re_im || n_gates < 0 || (n_gates > 0 && !gates)) return DMRGC_EINVAL;
   dmrgc_ctx* c = a;   // errors are reported on a
-  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64)
-    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid and storage precision");
+  if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64 || a->order != b->order)
+    return fail(a, DMRGC_EINVAL, "overlap needs contexts of the same grid, order and storage precision");
+  if (a->ng > 0 || b->ng > 0) return fail(a, DMRGC_EINVAL, "overlap: contexts with one qubit per tensor only");
   // the middle section's MPO lives in a scratch context on a's stream: o keeps
   // a's cuda_stream, so m->st == a->st and every ensure(m, ...) that grows a
   // buffer synchronises the stream the GEMMs below run on
@@ -1578,6 +1647,7 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
 
 dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed, unsigned char* out_bits) {
   if (!c) return DMRGC_EINVAL;
+  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "sample: contexts with one qubit per tensor only");
   if (count < 0 || (count > 0 && !out_bits)) return fail(c, DMRGC_EINVAL, "bad sample arguments");
   if (count == 0) return DMRGC_OK;
   if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
@@ -1653,6 +1723,7 @@ dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count
   if (sampled->N != reference->N || sampled->rows != reference->rows || sampled->cols != reference->cols)
     return fail(c, DMRGC_EINVAL, "xeb needs two contexts on the same grid");
   if (sampled->N > 62) return fail(c, DMRGC_EINVAL, "xeb: 2^N does not fit");
+  if (sampled->ng > 0 || reference->ng > 0) return fail(c, DMRGC_EINVAL, "xeb: contexts with one qubit per tensor only");
   const int N = sampled->N;
   std::vector<unsigned char> bits((size_t)count * N);
   TRY(dmrgc_sample(sampled, count, seed, bits.data()));
@@ -1676,18 +1747,20 @@ dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count
 dmrgc_status dmrgc_bond_dims(const dmrgc_ctx* c, int* mps_bonds, int* mpo_bonds) {
   if (!c) return DMRGC_EINVAL;
   const std::vector<int>& b = c->phase == 1 ? c->chiA : c->chiB;
-  for (int i = 0; i + 1 < c->N; ++i) {
+  const int nt = c->ng > 0 ? c->ng : c->N;
+  for (int i = 0; i + 1 < nt; ++i)
     if (mps_bonds) mps_bonds[i] = b[i + 1];
+  for (int i = 0; i + 1 < c->N; ++i)
     if (mpo_bonds) mpo_bonds[i] = c->D[i + 1];
-  }
   return DMRGC_OK;
 }
 
 long long dmrgc_mps_size(const dmrgc_ctx* c) {
   if (!c) return -1;
   const std::vector<int>& b = c->phase == 1 ? c->chiA : c->chiB;
+  const int nt = c->ng > 0 ? c->ng : c->N;
   long long s = 0;
-  for (int i = 0; i < c->N; ++i) s += 2LL * b[i] * b[i + 1];
+  for (int i = 0; i < nt; ++i) s += (1LL << c->gsize[i]) * b[i] * b[i + 1];
   return s;
 }
 
@@ -1696,9 +1769,10 @@ dmrgc_status dmrgc_get_mps(const dmrgc_ctx* cc, double* out_re_im, int* centre) 
   if (!c || !out_re_im) return DMRGC_EINVAL;
   std::vector<int>* bonds;
   auto& st = current_state(c, bonds);
+  const int nt = c->ng > 0 ? c->ng : c->N;
   long long off = 0;
-  for (int i = 0; i < c->N; ++i) {
-    const long long n = 2LL * (*bonds)[i] * (*bonds)[i + 1];
+  for (int i = 0; i < nt; ++i) {
+    const long long n = (1LL << c->gsize[i]) * (*bonds)[i] * (*bonds)[i + 1];
     TRY(ensure(c, c->stage_d, (size_t)n * sizeof(double2)));
     CK(to_complex128(st[i].p, n, c->fp64, (double2*)c->stage_d.p, c->st));
     CK(cudaMemcpyAsync(out_re_im + 2 * off, c->stage_d.p, (size_t)n * sizeof(double2),
@@ -1713,16 +1787,17 @@ dmrgc_status dmrgc_get_mps(const dmrgc_ctx* cc, double* out_re_im, int* centre) 
 dmrgc_status dmrgc_set_mps(dmrgc_ctx* c, const double* in_re_im, const int* bonds, double log_F_tilde) {
   if (!c) return DMRGC_EINVAL;
   if (!in_re_im || !bonds) return fail(c, DMRGC_EINVAL, "set_mps: null argument");
-  const int N = c->N;
+  const int N = c->ng > 0 ? c->ng : c->N;   // tensors
   if (bonds[0] != 1 || bonds[N] != 1) return fail(c, DMRGC_EINVAL, "set_mps: outer bonds must be 1");
   for (int i = 1; i < N; ++i)
     if (bonds[i] < 1 || bonds[i] > c->chi)
       return fail(c, DMRGC_EINVAL, "set_mps: bond " + std::to_string(i) + " out of range");
   for (int i = 0; i < N; ++i)
-    if ((long long)bonds[i] * bonds[i + 1] > (1ll << 26)) return fail(c, DMRGC_EINVAL, "set_mps: site too large");
+    if ((long long)bonds[i] * bonds[i + 1] * (1ll << c->gsize[i]) > (1ll << 27))
+      return fail(c, DMRGC_EINVAL, "set_mps: tensor too large");
   long long off = 0;
   for (int i = 0; i < N; ++i) {
-    const long long n = 2LL * bonds[i] * bonds[i + 1];
+    const long long n = (1LL << c->gsize[i]) * bonds[i] * bonds[i + 1];
     TRY(ensure(c, c->B[i], (size_t)n * c->esz));
     TRY(ensure(c, c->stage_d, (size_t)n * sizeof(double2)));
     CK(cudaMemcpyAsync(c->stage_d.p, in_re_im + 2 * off, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice,
@@ -1739,6 +1814,7 @@ dmrgc_status dmrgc_set_mps(dmrgc_ctx* c, const double* in_re_im, const int* bond
   c->hist.clear();
   c->L = EnvRef();
   c->R = EnvRef();
+  c->gsweep = 0;
   std::fill(c->xyk.begin(), c->xyk.end(), 0);
   return DMRGC_OK;
 }
@@ -1747,6 +1823,7 @@ dmrgc_status dmrgc_sweep_updates(dmrgc_ctx* c, long long n_updates, double* f_la
   if (!c) return DMRGC_EINVAL;
   if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep_updates before dmrgc_apply_layer");
   if (n_updates < 0) return fail(c, DMRGC_EINVAL, "n_updates < 0");
+  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "dmrgc_sweep_updates: two-site contexts only");
   TRY(run_updates(c, n_updates));
   if (f_last) *f_last = c->f_cur;
   return DMRGC_OK;
@@ -1863,7 +1940,7 @@ dmrgc_status dmrgc_test_svd_gram(int precision, int m, int n, const double* G, i
   g.C = dH; g.ldc = m;
   TcWork w;
   cudaError_t e = run_gemm(precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3, g, &w, err, 0);
-  if (e == cudaSuccess) e = eig_truncate(dH, m, chi, rel_cut, 0.0, 1e-4, work, res, dU, 0, 0, nullptr);
+  if (e == cudaSuccess) e = eig_truncate(dH, m, chi, rel_cut, 0.0, kEigResolve, work, res, dU, 0, 0, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   w.release();
   if (e != cudaSuccess) return DMRGC_ECUDA;

@@ -92,7 +92,8 @@ struct TruncResult {
   double f;       // sum of kept s^2
   double norm2;   // sum of all s^2
   int nnz;        // columns above the numerical-zero level (the rank found)
-  int pad2;
+  int by_cut;     // 1: k was set by the cutoff (fewer than min(chi, n) values above it)
+  double tail;    // (s_{k-1} / s_1)^2: the smallest kept Gram eigenvalue over the largest
 };
 size_t trunc_bytes(int n);  // TruncResult followed by double s[n], int perm[n]
 // fro2 / zero_rel: the Frobenius norm^2 of the matrix given to the Jacobi kernel
@@ -115,13 +116,16 @@ cudaError_t gather_columns(const void* W, int m, int n_total, int k, const void*
 // and writes res (TruncResult + s[n] + perm[n], as truncate_columns) and the
 // k leading eigenvectors to out: mode 0 out[r * k + v], mode 1 out[v * n + r],
 // mode 2 out[v * n + r] conjugated.  res->status: 0 done; 1 not resolved
-// (lambda_{k-1} < resolve * lambda_0 or the count set by the cut: use the
-// Jacobi SVD; nothing is written to out); DMRGC_ENUMERIC; DMRGC_ETIMEOUT.
+// (lambda_{k-1} < resolve * lambda_0, or the count set by a cut with
+// cut^2 < resolve: use the Jacobi SVD; nothing is written to out);
+// DMRGC_ENUMERIC; DMRGC_ETIMEOUT.
 size_t eig_work_bytes(int n, int kk);
 cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, double resolve, void* work,
                          void* res, void* out, int mode, cudaStream_t st, int* launches);
-// |x|^2 (complex64, FP64 sum in a fixed order) to *out_dev; x /= |x| if scale
-cudaError_t norm2_scale(void* x, long long n, double* out_dev, bool scale, cudaStream_t st);
+// |x|^2 (FP64 sum in a fixed order: the same bits on every run) to *out_dev;
+// x /= |x| if scale.  part_dev: 256 doubles of scratch.  Two kernels of 256 CTAs.
+cudaError_t norm2_scale(void* x, long long n, bool fp64, double* out_dev, double* part_dev, bool scale,
+                        cudaStream_t st);
 
 // Spectrum read-outs of a truncation result (k = kept count):
 // out32[j] = log10(s_mu^2 / sum_{nu<k} s_nu^2) at mu = round(j (k-1) / 31), j < 32;
@@ -133,6 +137,11 @@ cudaError_t rank_label(const void* res, int k, double frac, int* out, cudaStream
 // uniforms at counters ctr0 + 2j, ctr0 + 2j + 1 (entry j).
 cudaError_t fill_gaussian(void* dst, long long n, bool fp64, unsigned long long seed,
                           unsigned long long ctr0, cudaStream_t st);
+// n complex entries (2u - 1) + i (2u' - 1), u, u' the SplitMix64 uniforms at
+// counters ctr0 + 2j, ctr0 + 2j + 1 (entry j): the random guess of the
+// single-site variant (Sec. V.D.1).
+cudaError_t fill_unit_square(void* dst, long long n, bool fp64, unsigned long long seed,
+                             unsigned long long ctr0, cudaStream_t st);
 
 // Rank model (mlp.cu): BF16 copy of the FP32 parameters, and one inference
 // from 32 device floats (the spectrum summary) + 4 host extras.
@@ -203,5 +212,16 @@ cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, i
 cudaError_t sample_select(const void* W, const void* T, int B, int r, unsigned long long seed, long long row0, int n,
                           int site, int qubit, unsigned char* out, void* V, bool fp64, cudaStream_t st);
 cudaError_t amp_store(const void* V, int B, double2* out, bool fp64, cudaStream_t st);
+// Metropolis chains (App. C), step t of `steps` for C chains over n qubits:
+// metro_draw writes the proposals prop[C][n] and acceptance uniforms uacc[C]
+// (SplitMix64 at counters g (n + 1) + q and g (n + 1) + n, g = c (steps + 1) + t);
+// metro_step, given the proposals' amplitudes, moves chain c iff t = 0, its
+// weight pcur[c] is 0 or uacc[c] pcur[c] < |amp[c]|^2 (acc[c] counts moves
+// at t >= 1), and for t >= 1 writes its string to out[c][t - 1][n].
+cudaError_t metro_draw(unsigned char* prop, double* uacc, int C, int n, int steps, int t, unsigned long long seed,
+                       cudaStream_t st);
+cudaError_t metro_step(const unsigned char* prop, const double2* amp, const double* uacc, unsigned char* cur,
+                       double* pcur, long long* acc, unsigned char* out, int C, int n, int steps, int t,
+                       cudaStream_t st);
 
 }  // namespace dmrgc

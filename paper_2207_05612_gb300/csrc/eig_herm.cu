@@ -17,10 +17,11 @@
 //     complex64 arithmetic.  The reflectors follow the LAPACK zlarfg
 //     convention (complex tau, real beta), so T is real: the last one, of
 //     size 1, only makes the final off-diagonal real.
-//  2. tri_bisect_kernel and tri_invit_kernel: the leading eigenvalues of T by
-//     Sturm-count multisection (FP32, one warp per eigenvalue); their
-//     eigenvectors by inverse iteration in FP64 (the small core), with
-//     modified Gram-Schmidt inside clusters of close eigenvalues.
+//  2. tri_bisect_kernel, tri_invit_kernel, tri_cluster_kernel: the leading
+//     eigenvalues of T by Sturm-count multisection (FP32, one warp per
+//     eigenvalue); their eigenvectors by inverse iteration in FP64 (the small
+//     core), one thread per eigenvalue, then modified Gram-Schmidt inside
+//     clusters of close eigenvalues and the Rayleigh quotients.
 //  3. bt_wy_kernel and he_backtrans_kernel: eigenvector of H = Q z.  The
 //     reflectors are grouped in blocks of WY in compact WY form
 //     P_a .. P_{a+WY-1} = I - V Tb V^+ (Tb upper triangular), and each block is
@@ -30,9 +31,9 @@
 // the scale of theta.  The Gram squares the condition number: eigenvalues
 // carry an absolute error of about eps |H|, so singular values below ~1e-3
 // s_1 are not resolved.  The caller therefore uses this path only when the
-// kept eigenvalues all lie well above that level (lambda_{k-1} >= 1e-4
-// lambda_0); otherwise, or when the eigensolver meets a non-finite value, the
-// update falls back to the Jacobi SVD of theta itself.
+// kept eigenvalues all lie well above that level (lambda_{k-1} >= 1e-5
+// lambda_0, set by the caller); otherwise, or when the eigensolver meets a
+// non-finite value, the update falls back to the Jacobi SVD of theta itself.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -57,33 +58,33 @@ static_assert(sizeof(HeCtl) == 64, "control block layout");
 
 constexpr unsigned long long kHeSpinLimit = 20000000ull;   // x ~64 ns, about 1.3 s
 
-__device__ __forceinline__ bool he_grid_barrier(HeCtl* c, unsigned nblocks) {
+// Grid barrier of the tridiagonalisation: CTA b publishes step value v in
+// flags[b] after a fence over its writes; thread t < G then waits for
+// flags[t] >= v (bounded; on timeout or another CTA's error every thread of
+// the CTA returns false).  No atomic counter, so arrivals do not serialise.
+// G <= blockDim.x; flags zeroed before the launch.
+__device__ __forceinline__ bool he_flag_barrier(HeCtl* c, unsigned* flags, int G, unsigned v) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &c->gen;
-    volatile int* verr = &c->err;
-    const unsigned g = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(&c->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&c->count, 0u);
-      __threadfence();
-      atomicAdd(&c->gen, 1u);
-    } else {
-      unsigned long long it = 0;
-      while (*vgen == g) {
-        if (it > 2048) __nanosleep(32);
-        if (*verr != 0) break;
-        if (++it > kHeSpinLimit) {
-          atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
-          break;
-        }
+    *((volatile unsigned*)(flags + blockIdx.x)) = v;
+  }
+  int bad = 0;
+  if ((int)threadIdx.x < G) {
+    volatile unsigned* f = flags + threadIdx.x;
+    unsigned long long it = 0;
+    while (*f < v) {
+      if (it > 2048) __nanosleep(32);
+      if (*((volatile int*)&c->err) != 0) { bad = 1; break; }
+      if (++it > kHeSpinLimit) {
+        atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
+        bad = 1;
+        break;
       }
     }
     __threadfence();
   }
-  __syncthreads();
-  return *((volatile int*)&c->err) == 0;
+  return __syncthreads_or(bad) == 0;
 }
 
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
@@ -179,7 +180,7 @@ template <bool SMEM_ROWS>
 __global__ void __launch_bounds__(TD_THREADS, 1)
     he_tridiag_kernel(float2* __restrict__ S, int n, double* __restrict__ d, double* __restrict__ beta,
                       float2* __restrict__ tau, float2* __restrict__ pbuf, float2* __restrict__ rowbuf,
-                      float* __restrict__ part, HeCtl* ctl) {
+                      float* __restrict__ part, unsigned* __restrict__ flags, HeCtl* ctl) {
   extern __shared__ float2 sm[];
   float2* vb0 = sm;              // u of even steps
   float2* vb1 = sm + n;          // u of odd steps
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
     }
     const float tot = block_sum<TD_THREADS>(dot, red);
     if (tid == 0) part[(size_t)(j & 1) * G + cta] = tot;
-    if (!he_grid_barrier(ctl, (unsigned)G)) return;
+    if (!he_flag_barrier(ctl, flags, G, (unsigned)(j + 1))) return;
   }
   // trailing 2 x 2 block with the last pending update, and the 1 x 1 reflector
   // that makes its off-diagonal real (CTA 0)
@@ -429,27 +430,39 @@ __global__ void tri_bisect_kernel(const float* __restrict__ d, const float* __re
   if (lane == 0) lam[warp] = 0.5f * (lo + hi);
 }
 
-// Inverse iteration in FP64 for eigenvectors 0..kk-1 of T (scaled), one
-// thread per cluster of eigenvalues closer than clus_gap (consecutive gaps),
-// members processed in order with modified Gram-Schmidt against the earlier
-// members after every solve.  Factorisation of T - sigma I by Gaussian
+// Inverse iteration in FP64 for eigenvectors 0..kv-1 of T (scaled), one
+// thread per eigenvalue.  Factorisation of T - sigma I by Gaussian
 // elimination with partial pivoting (pivots below pivmin raised to pivmin),
-// reciprocal pivots stored.  A thread keeps its factors, its row swaps and its
-// vector in shared memory (5 n doubles + n bytes, blockDim.x threads per
-// CTA, element i of thread lt at [i * blockDim.x + lt]); the cluster's
-// finished vectors are read back from Z.  Z: n x kk doubles (element i of
-// vector v at Z[i * kk + v]).  lam_out: Rayleigh quotients (units of H).
-// Only vectors 0..kv-1 are computed (kv = the most the truncation can keep,
-// kk - 1 when kk = chi + 1: the extra eigenvalue only serves the cut rules and
+// reciprocal pivots stored; INVIT_ITERS solves, each followed by a
+// normalisation.  A thread keeps its factors, its row swaps and its vector in
+// shared memory (5 n doubles + n bytes, blockDim.x threads per CTA, element i
+// of thread lt at [i * blockDim.x + lt]).  Z: n x kk doubles (element i of
+// vector v at Z[i * kk + v]).  Eigenvalues closer than the bisection's
+// resolution give vectors that are not mutually orthogonal; tri_cluster_kernel
+// orthonormalises each such cluster afterwards (their span is the cluster's
+// invariant subspace, which is all the truncation uses) and forms the
+// Rayleigh quotients.  Only vectors 0..kv-1 are computed (kv = the most the
+// truncation can keep; the extra eigenvalue only serves the cut rules and
 // keeps its bisection value).  An eigenvalue below half the resolution level
 // (lam[v] < 0.5 resolve lam[0]) cannot belong to a resolved truncation: the
-// CTA flags the result unresolved and computes nothing more.
-constexpr int INVIT_ITERS = 3;
-constexpr int MAX_CLUSTER = 16;
+// thread flags the result unresolved and computes nothing more.
+constexpr int INVIT_ITERS = 2;
+constexpr int MAX_CLUSTER = 32;
+
+// 1 / a for 1e-15 <= |a| <= 1e30: an FP32 reciprocal refined by two
+// Newton-Raphson steps x <- x + x (1 - a x) in FP64 (each squares the
+// relative error: ~1e-7 -> ~1e-14 -> below FP64 rounding)
+__device__ __forceinline__ double recip_nr(double a) {
+  double x = (double)__frcp_rn((float)a);
+  double e = fma(-a, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-a, x, 1.0);
+  return fma(x, e, x);
+}
 
 __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __restrict__ e0, int n, int kk,
-                                 int kv, const float* __restrict__ lam, double clus_gap, double resolve,
-                                 double* __restrict__ Z, double* __restrict__ lam_out, HeCtl* ctl) {
+                                 int kv, const float* __restrict__ lam, double resolve, double* __restrict__ Z,
+                                 double* __restrict__ lam_out, HeCtl* ctl) {
   extern __shared__ double ivs[];
   const int IV = blockDim.x, lt = threadIdx.x;
   double* IU0 = ivs;                      // 1 / pivot
@@ -458,109 +471,151 @@ __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __
   double* L = ivs + (size_t)3 * n * IV;   // multipliers
   double* z = ivs + (size_t)4 * n * IV;
   unsigned char* swp = reinterpret_cast<unsigned char*>(ivs + (size_t)5 * n * IV);
-  const int v0 = blockIdx.x * IV + lt;
-  if (v0 >= kk) return;
+  const int v = blockIdx.x * IV + lt;
+  if (v >= kk) return;
   const double scale = (double)ctl->scale;
-  if (v0 >= kv) {   // the extra eigenvalue: bisection value only
-    lam_out[v0] = (double)lam[v0] * scale;
+  if (v >= kv) {   // the extra eigenvalue: bisection value only
+    lam_out[v] = (double)lam[v] * scale;
     return;
   }
-  if (v0 > 0 && (double)lam[v0 - 1] - (double)lam[v0] <= clus_gap) return;   // not a cluster leader
-  int v1 = v0 + 1;
-  while (v1 < kv && (double)lam[v1 - 1] - (double)lam[v1] <= clus_gap) ++v1;
-  if (v1 - v0 > MAX_CLUSTER || !((double)lam[v1 - 1] >= 0.5 * resolve * (double)lam[0])) {
+  if (!((double)lam[v] >= 0.5 * resolve * (double)lam[0])) {
     atomicExch(&ctl->status, 1);
     return;
   }
   const double inv_scale = 1.0 / scale;
   const double pivmin = 1e-15;
 #define IVX(arr, i) arr[(size_t)(i) * IV + lt]
-  for (int v = v0; v < v1; ++v) {
-    const double sigma = (double)lam[v];
-    // factorisation (scaled entries)
-    double ca = d0[0] * inv_scale - sigma;
-    double cb = n > 1 ? e0[0] * inv_scale : 0.0;
-    double ck = cb;   // subdiagonal of row k+1 = e_k
-    for (int k = 0; k + 1 < n; ++k) {
-      const double ak1 = d0[k + 1] * inv_scale - sigma;
-      const double bk1 = (k + 2 < n) ? e0[k + 1] * inv_scale : 0.0;
-      if (fabs(ca) >= fabs(ck)) {
-        double piv = ca;
-        if (fabs(piv) < pivmin) piv = piv < 0.0 ? -pivmin : pivmin;
-        const double ip = 1.0 / piv;
-        const double l = ck * ip;
-        IVX(IU0, k) = ip; IVX(U1, k) = cb; IVX(U2, k) = 0.0; IVX(L, k) = l; IVX(swp, k) = 0;
-        ca = ak1 - l * cb;
-        cb = bk1;
-      } else {
-        const double ip = 1.0 / ck;
-        const double l = ca * ip;
-        IVX(IU0, k) = ip; IVX(U1, k) = ak1; IVX(U2, k) = bk1; IVX(L, k) = l; IVX(swp, k) = 1;
-        ca = cb - l * ak1;
-        cb = -l * bk1;
-      }
-      ck = bk1;
-    }
-    {
+  const double sigma = (double)lam[v];
+  // factorisation (scaled entries)
+  double ca = d0[0] * inv_scale - sigma;
+  double cb = n > 1 ? e0[0] * inv_scale : 0.0;
+  double ck = cb;   // subdiagonal of row k+1 = e_k
+  for (int k = 0; k + 1 < n; ++k) {
+    const double ak1 = d0[k + 1] * inv_scale - sigma;
+    const double bk1 = (k + 2 < n) ? e0[k + 1] * inv_scale : 0.0;
+    if (fabs(ca) >= fabs(ck)) {
       double piv = ca;
       if (fabs(piv) < pivmin) piv = piv < 0.0 ? -pivmin : pivmin;
-      IVX(IU0, n - 1) = 1.0 / piv;
+      const double ip = recip_nr(piv);
+      const double l = ck * ip;
+      IVX(IU0, k) = ip; IVX(U1, k) = cb; IVX(U2, k) = 0.0; IVX(L, k) = l; IVX(swp, k) = 0;
+      ca = ak1 - l * cb;
+      cb = bk1;
+    } else {
+      const double ip = recip_nr(fabs(ck) < pivmin ? (ck < 0.0 ? -pivmin : pivmin) : ck);
+      const double l = ca * ip;
+      IVX(IU0, k) = ip; IVX(U1, k) = ak1; IVX(U2, k) = bk1; IVX(L, k) = l; IVX(swp, k) = 1;
+      ca = cb - l * ak1;
+      cb = -l * bk1;
     }
-    // start vector: a fixed pseudo-random sequence (integer hash of i, v)
-    for (int i = 0; i < n; ++i) {
-      unsigned h = (unsigned)i * 2654435761u ^ ((unsigned)v * 0x9E3779B9u + 0x7F4A7C15u);
-      h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-      IVX(z, i) = 0.5 + (double)(h & 0xFFFFu) / 65536.0;
-    }
-    for (int it = 0; it < INVIT_ITERS; ++it) {
-      // forward: the row operations of the elimination (y_k carried in a register)
-      double yk = IVX(z, 0);
-      for (int k = 0; k + 1 < n; ++k) {
-        double yk1 = IVX(z, k + 1);
-        const double l = IVX(L, k);
-        if (IVX(swp, k)) { const double t = yk; yk = yk1; yk1 = t - l * yk; }
-        else yk1 -= l * yk;
-        IVX(z, k) = yk;
-        yk = yk1;
-      }
-      IVX(z, n - 1) = yk;
-      // back substitution (x_{k+1}, x_{k+2} carried in registers)
-      double x2 = 0.0, x1 = 0.0;
-      for (int k = n - 1; k >= 0; --k) {
-        double y = IVX(z, k);
-        if (k + 1 < n) y -= IVX(U1, k) * x1;
-        if (k + 2 < n) y -= IVX(U2, k) * x2;
-        const double x = y * IVX(IU0, k);
-        IVX(z, k) = x;
-        x2 = x1;
-        x1 = x;
-      }
-      // orthogonalise against the earlier members of the cluster (finished in Z)
-      for (int q = v0; q < v; ++q) {
-        double dp = 0.0;
-        for (int i = 0; i < n; ++i) dp += Z[(size_t)i * kk + q] * IVX(z, i);
-        for (int i = 0; i < n; ++i) IVX(z, i) -= dp * Z[(size_t)i * kk + q];
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < n; ++i) { const double t = IVX(z, i); nrm += t * t; }
-      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-      for (int i = 0; i < n; ++i) IVX(z, i) *= inv;
-    }
-    // Rayleigh quotient z^T T z, and the vector to Z
-    double rq = 0.0, zp = 0.0, zc = IVX(z, 0);
-    for (int i = 0; i < n; ++i) {
-      const double zn = (i + 1 < n) ? IVX(z, i + 1) : 0.0;
-      double tz = d0[i] * zc;
-      if (i > 0) tz += e0[i - 1] * zp;
-      if (i + 1 < n) tz += e0[i] * zn;
-      rq += zc * tz;
-      Z[(size_t)i * kk + v] = zc;
-      zp = zc;
-      zc = zn;
-    }
-    lam_out[v] = rq;
+    ck = bk1;
   }
+  {
+    double piv = ca;
+    if (fabs(piv) < pivmin) piv = piv < 0.0 ? -pivmin : pivmin;
+    IVX(IU0, n - 1) = recip_nr(piv);
+  }
+  // start vector: a fixed pseudo-random sequence (integer hash of i, v)
+  for (int i = 0; i < n; ++i) {
+    unsigned h = (unsigned)i * 2654435761u ^ ((unsigned)v * 0x9E3779B9u + 0x7F4A7C15u);
+    h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+    IVX(z, i) = 0.5 + (double)(h & 0xFFFFu) / 65536.0;
+  }
+  for (int it = 0; it < INVIT_ITERS; ++it) {
+    // forward: the row operations of the elimination (y_k carried in a register)
+    double yk = IVX(z, 0);
+    for (int k = 0; k + 1 < n; ++k) {
+      double yk1 = IVX(z, k + 1);
+      const double l = IVX(L, k);
+      if (IVX(swp, k)) { const double t = yk; yk = yk1; yk1 = t - l * yk; }
+      else yk1 -= l * yk;
+      IVX(z, k) = yk;
+      yk = yk1;
+    }
+    IVX(z, n - 1) = yk;
+    // back substitution (x_{k+1}, x_{k+2} carried in registers), with the norm
+    double x2 = 0.0, x1 = 0.0, nrm = 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+      double y = IVX(z, k);
+      if (k + 1 < n) y -= IVX(U1, k) * x1;
+      if (k + 2 < n) y -= IVX(U2, k) * x2;
+      const double x = y * IVX(IU0, k);
+      IVX(z, k) = x;
+      nrm += x * x;
+      x2 = x1;
+      x1 = x;
+    }
+    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+    for (int i = 0; i < n; ++i) IVX(z, i) *= inv;
+  }
+  for (int i = 0; i < n; ++i) Z[(size_t)i * kk + v] = IVX(z, i);
 #undef IVX
+}
+
+// One CTA per eigenvalue index v < kv; the leader of each cluster (consecutive
+// eigenvalues closer than clus_gap, scaled units) orthonormalises the
+// cluster's vectors by modified Gram-Schmidt, twice, and every member gets its
+// Rayleigh quotient z^T T z (units of H) in lam_out.  Clusters longer than
+// MAX_CLUSTER flag the result unresolved.  256 threads.
+__global__ void __launch_bounds__(256) tri_cluster_kernel(const double* __restrict__ d0,
+                                                          const double* __restrict__ e0, int n, int kk, int kv,
+                                                          const float* __restrict__ lam, double clus_gap,
+                                                          double* __restrict__ Z, double* __restrict__ lam_out,
+                                                          HeCtl* ctl) {
+  __shared__ double red[8];
+  __shared__ int s_status;
+  const int v0 = blockIdx.x, tid = threadIdx.x;
+  if (tid == 0) s_status = *((volatile int*)&ctl->status);
+  __syncthreads();
+  if (v0 >= kv || s_status != 0) return;   // uniform per CTA
+  if (v0 > 0 && (double)lam[v0 - 1] - (double)lam[v0] <= clus_gap) return;   // not a cluster leader
+  int v1 = v0 + 1;
+  while (v1 < kv && (double)lam[v1 - 1] - (double)lam[v1] <= clus_gap) ++v1;
+  if (v1 - v0 > MAX_CLUSTER) {
+    if (tid == 0) atomicExch(&ctl->status, 1);
+    return;
+  }
+  auto block_sum = [&](double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    return t;
+  };
+  if (v1 - v0 > 1) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int v = v0; v < v1; ++v) {
+        for (int q = v0; q < v; ++q) {
+          double dp = 0.0;
+          for (int i = tid; i < n; i += 256) dp += Z[(size_t)i * kk + q] * Z[(size_t)i * kk + v];
+          dp = block_sum(dp);
+          for (int i = tid; i < n; i += 256) Z[(size_t)i * kk + v] -= dp * Z[(size_t)i * kk + q];
+          __syncthreads();
+        }
+        double nr = 0.0;
+        for (int i = tid; i < n; i += 256) { const double t = Z[(size_t)i * kk + v]; nr += t * t; }
+        nr = block_sum(nr);
+        const double inv = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+        for (int i = tid; i < n; i += 256) Z[(size_t)i * kk + v] *= inv;
+        __syncthreads();
+      }
+  }
+  for (int v = v0; v < v1; ++v) {   // Rayleigh quotient with the unscaled T
+    double rq = 0.0;
+    for (int i = tid; i < n; i += 256) {
+      const double zi = Z[(size_t)i * kk + v];
+      double tz = d0[i] * zi;
+      if (i > 0) tz += e0[i - 1] * Z[(size_t)(i - 1) * kk + v];
+      if (i + 1 < n) tz += e0[i] * Z[(size_t)(i + 1) * kk + v];
+      rq += zi * tz;
+    }
+    rq = block_sum(rq);
+    if (tid == 0) lam_out[v] = rq;
+  }
 }
 
 // Truncation from the eigenvalues (kk = min(chi + 1, n) leading ones, in the
@@ -569,8 +624,9 @@ __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __
 // spectrum read-outs work unchanged: k = min(chi, n, #{s > cut s_1}); with
 // tie_rel > 0 a cut inside a multiplet (s_{k-1} - s_k <= tie_rel s_1) moves
 // down to the multiplet's upper edge.  status 0: every kept eigenvalue is
-// resolved (lambda_{k-1} >= resolve lambda_0) and the count was not set by
-// the cut; 1: not resolved; 2: the eigensolver met a non-finite value (both:
+// resolved (lambda_{k-1} >= resolve lambda_0) and the count was not set by a
+// cut below the resolution level (cut^2 < resolve: the sweep's cut, not the
+// zip-up's); 1: not resolved; 2: the eigensolver met a non-finite value (both:
 // the caller falls back to the Jacobi SVD); DMRGC_ETIMEOUT: a grid-barrier
 // wait ran out.  One CTA of 1024.
 __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restrict__ lam, int n, int kk, int chi,
@@ -578,7 +634,6 @@ __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restric
                                                          const double* __restrict__ d0, TruncResult* res,
                                                          HeCtl* ctl) {
   __shared__ double red[32];
-  __shared__ int s_k, s_bycut;
   double* s = reinterpret_cast<double*>(res + 1);
   int* perm = reinterpret_cast<int*>(s + n);
   const int tid = threadIdx.x;
@@ -619,7 +674,9 @@ __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restric
     if (ctl->err != 0) st = (int)DMRGC_ETIMEOUT;
     else if (ctl->status != 0) st = 1;
     else if (bad || !isfinite(f) || !isfinite(tot)) st = 2;
-    else if (by_cut || !(lam[k - 1] >= resolve * lam[0]) || !(lam[0] > 0.0)) st = 1;
+    // a count set by the cut is trusted only when the cut itself (cut^2 in
+    // eigenvalue units) lies at or above the resolution level
+    else if ((by_cut && cut * cut < resolve) || !(lam[k - 1] >= resolve * lam[0]) || !(lam[0] > 0.0)) st = 1;
     res->k = k;
     res->n = n;
     res->status = st;
@@ -627,9 +684,8 @@ __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restric
     res->f = f;
     res->norm2 = tot;
     res->nnz = k;
-    res->pad2 = 0;
-    s_k = k;
-    s_bycut = by_cut;
+    res->by_cut = by_cut;
+    res->tail = s[0] > 0.0 ? (s[k - 1] / s[0]) * (s[k - 1] / s[0]) : 0.0;
   }
 }
 
@@ -699,7 +755,7 @@ __global__ void __launch_bounds__(256) bt_wy_kernel(const float2* __restrict__ S
 // y -= V c.  The block's columns are staged in shared memory by the CTA.
 // Output: mode 0: out[r * k + v] = y_r; mode 1: out[v * n + r] = y_r;
 // mode 2: out[v * n + r] = conj(y_r).
-constexpr int BT_WARPS = 8;
+constexpr int BT_WARPS = 4;
 
 template <int E>
 __global__ void __launch_bounds__(BT_WARPS * 32)
@@ -740,11 +796,12 @@ __global__ void __launch_bounds__(BT_WARPS * 32)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (32 * e + 31 <= a) continue;   // rows <= a: every column of the block is zero there
+      const float2 ys = make_float2(y[e].y, y[e].x);
 #pragma unroll
-      for (int i = 0; i < WY; ++i) {
-        const float2 q = f2cmul(vsh[i * 32 * E + lane + 32 * e], y[e]);
-        c[i].x += q.x;
-        c[i].y += q.y;
+      for (int i = 0; i < WY; ++i) {   // c_i += conj(v) y, two packed FMAs
+        const float2 vv = vsh[i * 32 * E + lane + 32 * e];
+        c[i] = __ffma2_rn(make_float2(vv.x, vv.x), y[e], c[i]);
+        c[i] = __ffma2_rn(make_float2(vv.y, -vv.y), ys, c[i]);
       }
     }
 #pragma unroll
@@ -771,10 +828,10 @@ __global__ void __launch_bounds__(BT_WARPS * 32)
     for (int e = 0; e < E; ++e) {
       if (32 * e + 31 <= a) continue;
 #pragma unroll
-      for (int i = 0; i < WY; ++i) {
-        const float2 q = f2mul(vsh[i * 32 * E + lane + 32 * e], tc[i]);
-        y[e].x -= q.x;
-        y[e].y -= q.y;
+      for (int i = 0; i < WY; ++i) {   // y -= v tc, two packed FMAs
+        const float2 vv = vsh[i * 32 * E + lane + 32 * e];
+        y[e] = __ffma2_rn(make_float2(-vv.x, -vv.x), tc[i], y[e]);
+        y[e] = __ffma2_rn(make_float2(vv.y, -vv.y), make_float2(tc[i].y, tc[i].x), y[e]);
       }
     }
   }
@@ -787,34 +844,6 @@ __global__ void __launch_bounds__(BT_WARPS * 32)
       else if (mode == 1) out[(size_t)v * n + r] = y[e];
       else out[(size_t)v * n + r] = make_float2(y[e].x, -y[e].y);
     }
-  }
-}
-
-// |x|^2 of a complex64 vector in FP64 by one CTA in a fixed order (the same
-// bits from run to run), written to *out; then x /= sqrt(*out) when scale.
-__global__ void __launch_bounds__(1024) norm2_scale_kernel(float2* __restrict__ x, long long n,
-                                                           double* __restrict__ out, int scale) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += 1024) s += (double)x[i].x * x[i].x + (double)x[i].y * x[i].y;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = red[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  const double tot = red[0];
-  if (threadIdx.x == 0) *out = tot;
-  if (!scale) return;
-  const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
-  for (long long i = threadIdx.x; i < n; i += 1024) {
-    float2 v = x[i];
-    x[i] = make_float2(v.x * inv, v.y * inv);
   }
 }
 
@@ -832,7 +861,7 @@ EigParts eig_parts(int n, int kk) {
   const size_t sizes[kParts] = {sizeof(HeCtl),                            // ctl
                                 (size_t)2 * n * sizeof(float2),           // pbuf
                                 (size_t)3 * n * sizeof(float2),           // rowbuf
-                                (size_t)2 * 1024 * sizeof(float),         // partial sums (<= 1024 CTAs)
+                                (size_t)3 * 1024 * sizeof(float),         // partial sums, barrier flags (<= 1024 CTAs)
                                 (size_t)n * sizeof(double),               // d
                                 (size_t)n * sizeof(double),               // e (= beta)
                                 (size_t)n * sizeof(double),               // lam (Rayleigh quotients)
@@ -854,11 +883,6 @@ EigParts eig_parts(int n, int kk) {
 
 }  // namespace
 
-cudaError_t norm2_scale(void* x, long long n, double* out_dev, bool scale, cudaStream_t st) {
-  norm2_scale_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<float2*>(x), n, out_dev, scale ? 1 : 0);
-  return cudaGetLastError();
-}
-
 size_t eig_work_bytes(int n, int kk) { return eig_parts(n, kk).total; }
 
 cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, double resolve, void* work,
@@ -871,6 +895,7 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   float2* pbuf = reinterpret_cast<float2*>(w + P.off[1]);
   float2* rowbuf = reinterpret_cast<float2*>(w + P.off[2]);
   float* part = reinterpret_cast<float*>(w + P.off[3]);
+  unsigned* flags = reinterpret_cast<unsigned*>(part + 2 * 1024);
   double* d = reinterpret_cast<double*>(w + P.off[4]);
   double* e = reinterpret_cast<double*>(w + P.off[5]);
   double* lam = reinterpret_cast<double*>(w + P.off[6]);
@@ -882,6 +907,7 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   double* Z = reinterpret_cast<double*>(w + P.off[12]);
   cudaError_t e_ = cudaMemsetAsync(ctl, 0, sizeof(HeCtl), st);
   if (e_ != cudaSuccess) return e_;
+  if ((e_ = cudaMemsetAsync(flags, 0, 1024 * sizeof(unsigned), st)) != cudaSuccess) return e_;
   float2* S = reinterpret_cast<float2*>(H);
   gram_scale_kernel<<<1, 1024, 0, st>>>(S, n, ctl);
   if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
@@ -904,10 +930,11 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   int per_sm = 0;
   if ((e_ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, TD_THREADS, dsm)) != cudaSuccess) return e_;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (!smem_rows) G = std::min(sms * per_sm, std::min(1024, std::max(1, n / 8)));
+  if (!smem_rows) G = std::min(sms * per_sm, std::min(TD_THREADS, std::max(1, n / 8)));
+  if (G > TD_THREADS) return cudaErrorInvalidConfiguration;   // one barrier flag per thread
   {
     int nn = n;
-    void* args[] = {&S, &nn, &d, &e, &tau, &pbuf, &rowbuf, &part, &ctl};
+    void* args[] = {&S, &nn, &d, &e, &tau, &pbuf, &rowbuf, &part, &flags, &ctl};
     e_ = cudaLaunchCooperativeKernel(tfn, dim3(G), dim3(TD_THREADS), args, dsm, st);
     if (e_ != cudaSuccess) return e_;
   }
@@ -926,7 +953,9 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
     const size_t ism = per_thread * iv;
     if ((e_ = allow_dyn_smem((const void*)tri_invit_kernel)) != cudaSuccess) return e_;
     const int kv = kk > chi ? chi : kk;   // vectors the truncation can keep
-    tri_invit_kernel<<<(kk + iv - 1) / iv, iv, ism, st>>>(d, e, n, kk, kv, lam32, 3e-5, resolve, Z, lam, ctl);
+    tri_invit_kernel<<<(kk + iv - 1) / iv, iv, ism, st>>>(d, e, n, kk, kv, lam32, resolve, Z, lam, ctl);
+    if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
+    tri_cluster_kernel<<<kv, 256, 0, st>>>(d, e, n, kk, kv, lam32, 3e-5, Z, lam, ctl);
     if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
   }
   TruncResult* tr = reinterpret_cast<TruncResult*>(res);
@@ -955,7 +984,7 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
     e_ = cudaLaunchKernel(fn, dim3((kk + BT_WARPS - 1) / BT_WARPS), dim3(BT_WARPS * 32), args, bsm, st);
     if (e_ != cudaSuccess) return e_;
   }
-  if (launches) *launches += 9;
+  if (launches) *launches += 10;
   return cudaSuccess;
 }
 

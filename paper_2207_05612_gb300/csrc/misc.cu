@@ -84,6 +84,51 @@ __global__ void sum_abs2_kernel(const C2* __restrict__ x, long long n, double* o
   }
 }
 
+// |x|^2 in FP64 in a fixed order: CTA b sums the chunk [b chunk, (b+1) chunk)
+// (thread, warp and CTA trees fixed), then every CTA of the second kernel adds
+// the kNormParts partials in the same fixed order, so every CTA and every run
+// sees the same bits.
+constexpr int kNormParts = 256;
+
+__device__ __forceinline__ double block256_sum(double s, double* red) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += red[w];
+  return t;
+}
+
+template <typename C2>
+__global__ void __launch_bounds__(256) norm2_part_kernel(const C2* __restrict__ x, long long n, long long chunk,
+                                                         double* __restrict__ part) {
+  __shared__ double red[8];
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += 256) s += (double)x[i].x * x[i].x + (double)x[i].y * x[i].y;
+  s = block256_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename C2>
+__global__ void __launch_bounds__(256) norm2_finish_kernel(C2* __restrict__ x, long long n, long long chunk,
+                                                           const double* __restrict__ part, double* __restrict__ out,
+                                                           int scale) {
+  __shared__ double red[8];
+  const double tot = block256_sum(part[threadIdx.x], red);   // blockDim == kNormParts
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out = tot;
+  if (!scale) return;
+  const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+    C2 v = x[i];
+    v.x = (decltype(v.x))(v.x * inv);
+    v.y = (decltype(v.y))(v.y * inv);
+    x[i] = v;
+  }
+}
+
 template <typename C2>
 __global__ void scale_kernel(C2* __restrict__ x, long long n, const double* norm2) {
   const double nrm = sqrt(*norm2);
@@ -158,7 +203,26 @@ __global__ void gaussian_kernel(C2* __restrict__ out, long long n, unsigned long
   }
 }
 
+template <typename C2>
+__global__ void unit_square_kernel(C2* __restrict__ out, long long n, unsigned long long seed,
+                                   unsigned long long ctr0) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    out[j].x = 2.0 * mix_uniform(seed, ctr0 + 2ull * j) - 1.0;
+    out[j].y = 2.0 * mix_uniform(seed, ctr0 + 2ull * j + 1ull) - 1.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t fill_unit_square(void* dst, long long n, bool fp64, unsigned long long seed,
+                             unsigned long long ctr0, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  if (fp64) unit_square_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<double2*>(dst), n, seed, ctr0);
+  else unit_square_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<float2*>(dst), n, seed, ctr0);
+  return cudaGetLastError();
+}
 
 cudaError_t fill_gaussian(void* dst, long long n, bool fp64, unsigned long long seed,
                           unsigned long long ctr0, cudaStream_t st) {
@@ -247,6 +311,19 @@ cudaError_t sum_abs2(const void* x, long long n, bool fp64, double* out_dev, cud
   if (b > 1024) b = 1024;
   if (fp64) sum_abs2_kernel<<<b, 256, 0, st>>>((const double2*)x, n, out_dev);
   else sum_abs2_kernel<<<b, 256, 0, st>>>((const float2*)x, n, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t norm2_scale(void* x, long long n, bool fp64, double* out_dev, double* part_dev, bool scale,
+                        cudaStream_t st) {
+  const long long chunk = (n + kNormParts - 1) / kNormParts;
+  if (fp64) {
+    norm2_part_kernel<<<kNormParts, 256, 0, st>>>((const double2*)x, n, chunk, part_dev);
+    norm2_finish_kernel<<<kNormParts, 256, 0, st>>>((double2*)x, n, chunk, part_dev, out_dev, scale ? 1 : 0);
+  } else {
+    norm2_part_kernel<<<kNormParts, 256, 0, st>>>((const float2*)x, n, chunk, part_dev);
+    norm2_finish_kernel<<<kNormParts, 256, 0, st>>>((float2*)x, n, chunk, part_dev, out_dev, scale ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 

@@ -8,6 +8,8 @@
 // i >= c, built from the right for i < c).  Bit i of sample j is 0 iff
 // u < p(0 | prefix), u from SplitMix64 (Steele, Lea, Flood 2014) evaluated at
 // counter j*N + i; probabilities accumulate in double.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dmrgc {
@@ -111,6 +113,46 @@ __global__ void ones_kernel(C2* __restrict__ V, int B) {
   if (b < B) V[b] = C2{1, 0};
 }
 
+// Metropolis chains (App. C): counters g (n + 1) + q (bit q, qubit order,
+// 1 iff u >= 1/2) and g (n + 1) + n (acceptance), g = chain (steps + 1) + t.
+__global__ void metro_draw_kernel(unsigned char* __restrict__ prop, double* __restrict__ uacc, int C, int n,
+                                  int steps, int t, unsigned long long seed) {
+  const long long total = (long long)C * (n + 1);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k / (n + 1)), q = (int)(k % (n + 1));
+    const unsigned long long g = (unsigned long long)c * (steps + 1) + t;
+    const double u = splitmix64_uniform(seed, g * (n + 1) + q);
+    if (q < n) prop[(size_t)c * n + q] = u >= 0.5 ? 1 : 0;
+    else uacc[c] = u;
+  }
+}
+
+// t = 0: the chain takes its draw; t >= 1: it moves to the proposal iff
+// u p(x) < p(x') (p(x) = 0 always moves); the chain's string after step t is
+// written to out[c][t - 1].
+__global__ void metro_step_kernel(const unsigned char* __restrict__ prop, const double2* __restrict__ amp,
+                                  const double* __restrict__ uacc, unsigned char* __restrict__ cur,
+                                  double* __restrict__ pcur, long long* __restrict__ acc,
+                                  unsigned char* __restrict__ out, int C, int n, int steps, int t) {
+  const int c = blockIdx.x;
+  if (c >= C) return;
+  __shared__ int move;
+  if (threadIdx.x == 0) {
+    const double q = amp[c].x * amp[c].x + amp[c].y * amp[c].y;
+    move = t == 0 || pcur[c] == 0.0 || uacc[c] * pcur[c] < q;
+    if (move) {
+      pcur[c] = q;
+      if (t > 0) acc[c] += 1;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    if (move) cur[(size_t)c * n + q] = prop[(size_t)c * n + q];
+    if (t > 0) out[((size_t)c * steps + (t - 1)) * n + q] = cur[(size_t)c * n + q];
+  }
+}
+
 }  // namespace
 
 cudaError_t readout_start(void* V, int B, bool fp64, cudaStream_t st) {
@@ -148,6 +190,25 @@ cudaError_t sample_select(const void* W, const void* T, int B, int r, unsigned l
 cudaError_t amp_store(const void* V, int B, double2* out, bool fp64, cudaStream_t st) {
   if (fp64) amp_store_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2*>(V), B, out);
   else amp_store_kernel<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float2*>(V), B, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dmrgc
+
+namespace dmrgc {
+
+cudaError_t metro_draw(unsigned char* prop, double* uacc, int C, int n, int steps, int t, unsigned long long seed,
+                       cudaStream_t st) {
+  const long long total = (long long)C * (n + 1);
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  metro_draw_kernel<<<blocks, 256, 0, st>>>(prop, uacc, C, n, steps, t, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t metro_step(const unsigned char* prop, const double2* amp, const double* uacc, unsigned char* cur,
+                       double* pcur, long long* acc, unsigned char* out, int C, int n, int steps, int t,
+                       cudaStream_t st) {
+  metro_step_kernel<<<C, 64, 0, st>>>(prop, amp, uacc, cur, pcur, acc, out, C, n, steps, t);
   return cudaGetLastError();
 }
 

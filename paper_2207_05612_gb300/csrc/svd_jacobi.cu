@@ -906,6 +906,8 @@ __global__ void sort_trunc_kernel(TruncResult* res, double* s, int* perm, const 
     res->f = f;
     res->norm2 = tot;
     res->nnz = nnz;
+    res->by_cut = k < (chi < n ? chi : n) ? 1 : 0;
+    res->tail = s1 > 0.0 ? (v[k - 1] / s1) * (v[k - 1] / s1) : 0.0;
   }
 }
 

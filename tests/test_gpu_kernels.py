@@ -227,7 +227,7 @@ def test_gram_eigensolver_svd_against_lapack(prec, m, n):
 
 
 def test_gram_eigensolver_declines_unresolved_spectra():
-    """A kept spectrum reaching below 1e-2 s_1 (1e-4 of the largest Gram
+    """A kept spectrum reaching below 3e-3 s_1 (1e-5 of the largest Gram
     eigenvalue) is left to the Jacobi SVD: k = -1."""
     from paper_2207_05612_gb300 import binding
     rng = np.random.default_rng(3)
@@ -242,6 +242,15 @@ def test_gram_eigensolver_declines_unresolved_spectra():
     g2 = _rand(rng, (m, 100)) @ _rand(rng, (100, n))
     _, k2, _ = binding.dmrgc_test_svd_gram(2, g2, 256, 2e-5)
     assert k2 == -1
+    # ... which is trusted when the cut lies above the resolution level (the
+    # zip-up's 4e-3: cut^2 = 1.6e-5 >= 1e-5): rank 100, spectrum 1 .. 0.1
+    s3 = np.linspace(1.0, 0.1, 100)
+    g3 = (u[:, :100] * s3) @ v[:, :100].conj().T
+    s_out, k3, u3 = binding.dmrgc_test_svd_gram(2, g3, 256, 4e-3)
+    assert k3 == 100
+    assert np.abs(u3.conj().T @ u3 - np.eye(100)).max() < 1e-4
+    proj = np.linalg.norm(u3.conj().T @ u[:, :100], axis=0)
+    assert proj.min() > 1 - 1e-4
 
 
 def test_gram_eigensolver_degenerate_spectrum():

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     from paper_2207_05612_gb300 import binding
     assert ctypes.sizeof(binding.Gate) == 8 + 32 * 8
-    assert ctypes.sizeof(binding.Stats) == 15 * 8
+    assert ctypes.sizeof(binding.Stats) == 16 * 8
     assert binding.MLP_PARAMS == 21377
     o = binding.dmrgc_default_options()      # host-only entry point
     assert o.precision == binding.DMRGC_FP64 and o.max_jacobi_sweeps == 40
@@ -65,7 +65,7 @@ def test_batch_item_layout_and_host_validation():
         ("n_workers", lambda it: None, 0),
         ("chi", lambda it: setattr(it, "chi", 0), 1),
         ("grid", lambda it: setattr(it, "grid_view", binding.Grid(3, 2, 0)), 1),
-        ("order", lambda it: setattr(it, "grid_view", binding.Grid(2, 3, 1)), 1),
+        ("order", lambda it: setattr(it, "grid_view", binding.Grid(2, 3, 3)), 1),
         ("sweeps", lambda it: setattr(it, "n_sweeps", -1), 1),
         ("gates", lambda it: setattr(it, "gates", None), 1),
     ]
