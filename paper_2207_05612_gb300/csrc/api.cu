@@ -1368,6 +1368,9 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
   }
   c->hist.clear();
   c->layer_no++;
+  // a new layer changes every spectrum: the first visit of each bond tries
+  // the eigensolver again
+  std::fill(c->eig_ok.begin(), c->eig_ok.end(), 1);
   TRY(build_mpo(c, gates, n_gates));
   if (c->ng > 0) {   // single-site variant: random guess in orthogonal form
     TRY(grouped_guess(c));

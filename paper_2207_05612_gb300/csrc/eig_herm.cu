@@ -58,33 +58,33 @@ static_assert(sizeof(HeCtl) == 64, "control block layout");
 
 constexpr unsigned long long kHeSpinLimit = 20000000ull;   // x ~64 ns, about 1.3 s
 
-// Grid barrier of the tridiagonalisation: CTA b publishes step value v in
-// flags[b] after a fence over its writes; thread t < G then waits for
-// flags[t] >= v (bounded; on timeout or another CTA's error every thread of
-// the CTA returns false).  No atomic counter, so arrivals do not serialise.
-// G <= blockDim.x; flags zeroed before the launch.
-__device__ __forceinline__ bool he_flag_barrier(HeCtl* c, unsigned* flags, int G, unsigned v) {
+__device__ __forceinline__ bool he_grid_barrier(HeCtl* c, unsigned nblocks) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &c->gen;
+    volatile int* verr = &c->err;
+    const unsigned g = *vgen;
     __threadfence();
-    *((volatile unsigned*)(flags + blockIdx.x)) = v;
-  }
-  int bad = 0;
-  if ((int)threadIdx.x < G) {
-    volatile unsigned* f = flags + threadIdx.x;
-    unsigned long long it = 0;
-    while (*f < v) {
-      if (it > 2048) __nanosleep(32);
-      if (*((volatile int*)&c->err) != 0) { bad = 1; break; }
-      if (++it > kHeSpinLimit) {
-        atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
-        bad = 1;
-        break;
+    const unsigned arrived = atomicAdd(&c->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&c->count, 0u);
+      __threadfence();
+      atomicAdd(&c->gen, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (*vgen == g) {
+        if (it > 2048) __nanosleep(32);
+        if (*verr != 0) break;
+        if (++it > kHeSpinLimit) {
+          atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
+          break;
+        }
       }
     }
     __threadfence();
   }
-  return __syncthreads_or(bad) == 0;
+  __syncthreads();
+  return *((volatile int*)&c->err) == 0;
 }
 
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
@@ -180,7 +180,7 @@ template <bool SMEM_ROWS>
 __global__ void __launch_bounds__(TD_THREADS, 1)
     he_tridiag_kernel(float2* __restrict__ S, int n, double* __restrict__ d, double* __restrict__ beta,
                       float2* __restrict__ tau, float2* __restrict__ pbuf, float2* __restrict__ rowbuf,
-                      float* __restrict__ part, unsigned* __restrict__ flags, HeCtl* ctl) {
+                      float* __restrict__ part, HeCtl* ctl) {
   extern __shared__ float2 sm[];
   float2* vb0 = sm;              // u of even steps
   float2* vb1 = sm + n;          // u of odd steps
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
     }
     const float tot = block_sum<TD_THREADS>(dot, red);
     if (tid == 0) part[(size_t)(j & 1) * G + cta] = tot;
-    if (!he_flag_barrier(ctl, flags, G, (unsigned)(j + 1))) return;
+    if (!he_grid_barrier(ctl, (unsigned)G)) return;
   }
   // trailing 2 x 2 block with the last pending update, and the 1 x 1 reflector
   // that makes its off-diagonal real (CTA 0)
@@ -441,11 +441,13 @@ __global__ void tri_bisect_kernel(const float* __restrict__ d, const float* __re
 // resolution give vectors that are not mutually orthogonal; tri_cluster_kernel
 // orthonormalises each such cluster afterwards (their span is the cluster's
 // invariant subspace, which is all the truncation uses) and forms the
-// Rayleigh quotients.  Only vectors 0..kv-1 are computed (kv = the most the
-// truncation can keep; the extra eigenvalue only serves the cut rules and
-// keeps its bisection value).  An eigenvalue below half the resolution level
-// (lam[v] < 0.5 resolve lam[0]) cannot belong to a resolved truncation: the
-// thread flags the result unresolved and computes nothing more.
+// Rayleigh quotients.  Only vectors 0..kv-1 above the cut (lam[v] > cut2
+// lam[0], cut2 = the cut on s squared) are computed: kv is the most the
+// truncation can keep, and the extra eigenvalue and those below the cut keep
+// their bisection values.  A computed eigenvalue below half the resolution
+// level (lam[v] < 0.5 resolve lam[0]) cannot belong to a resolved
+// truncation: the thread flags the result unresolved and computes nothing
+// more.
 constexpr int INVIT_ITERS = 2;
 constexpr int MAX_CLUSTER = 32;
 
@@ -461,8 +463,8 @@ __device__ __forceinline__ double recip_nr(double a) {
 }
 
 __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __restrict__ e0, int n, int kk,
-                                 int kv, const float* __restrict__ lam, double resolve, double* __restrict__ Z,
-                                 double* __restrict__ lam_out, HeCtl* ctl) {
+                                 int kv, const float* __restrict__ lam, double cut2, double resolve,
+                                 double* __restrict__ Z, double* __restrict__ lam_out, HeCtl* ctl) {
   extern __shared__ double ivs[];
   const int IV = blockDim.x, lt = threadIdx.x;
   double* IU0 = ivs;                      // 1 / pivot
@@ -474,7 +476,8 @@ __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __
   const int v = blockIdx.x * IV + lt;
   if (v >= kk) return;
   const double scale = (double)ctl->scale;
-  if (v >= kv) {   // the extra eigenvalue: bisection value only
+  if (v >= kv || !((double)lam[v] > cut2 * (double)lam[0])) {
+    // the extra eigenvalue, or one below the cut (never kept): bisection value only
     lam_out[v] = (double)lam[v] * scale;
     return;
   }
@@ -552,25 +555,27 @@ __global__ void tri_invit_kernel(const double* __restrict__ d0, const double* __
 #undef IVX
 }
 
-// One CTA per eigenvalue index v < kv; the leader of each cluster (consecutive
-// eigenvalues closer than clus_gap, scaled units) orthonormalises the
+// One CTA per eigenvalue index v < kv above the cut; the leader of each
+// cluster (consecutive computed eigenvalues closer than clus_gap, scaled
+// units) orthonormalises the
 // cluster's vectors by modified Gram-Schmidt, twice, and every member gets its
 // Rayleigh quotient z^T T z (units of H) in lam_out.  Clusters longer than
 // MAX_CLUSTER flag the result unresolved.  256 threads.
 __global__ void __launch_bounds__(256) tri_cluster_kernel(const double* __restrict__ d0,
                                                           const double* __restrict__ e0, int n, int kk, int kv,
-                                                          const float* __restrict__ lam, double clus_gap,
-                                                          double* __restrict__ Z, double* __restrict__ lam_out,
-                                                          HeCtl* ctl) {
+                                                          const float* __restrict__ lam, double cut2,
+                                                          double clus_gap, double* __restrict__ Z,
+                                                          double* __restrict__ lam_out, HeCtl* ctl) {
   __shared__ double red[8];
   __shared__ int s_status;
   const int v0 = blockIdx.x, tid = threadIdx.x;
   if (tid == 0) s_status = *((volatile int*)&ctl->status);
   __syncthreads();
-  if (v0 >= kv || s_status != 0) return;   // uniform per CTA
+  const double lcut = cut2 * (double)lam[0];
+  if (v0 >= kv || s_status != 0 || !((double)lam[v0] > lcut)) return;   // uniform per CTA
   if (v0 > 0 && (double)lam[v0 - 1] - (double)lam[v0] <= clus_gap) return;   // not a cluster leader
   int v1 = v0 + 1;
-  while (v1 < kv && (double)lam[v1 - 1] - (double)lam[v1] <= clus_gap) ++v1;
+  while (v1 < kv && (double)lam[v1] > lcut && (double)lam[v1 - 1] - (double)lam[v1] <= clus_gap) ++v1;
   if (v1 - v0 > MAX_CLUSTER) {
     if (tid == 0) atomicExch(&ctl->status, 1);
     return;
@@ -861,7 +866,7 @@ EigParts eig_parts(int n, int kk) {
   const size_t sizes[kParts] = {sizeof(HeCtl),                            // ctl
                                 (size_t)2 * n * sizeof(float2),           // pbuf
                                 (size_t)3 * n * sizeof(float2),           // rowbuf
-                                (size_t)3 * 1024 * sizeof(float),         // partial sums, barrier flags (<= 1024 CTAs)
+                                (size_t)2 * 1024 * sizeof(float),         // partial sums (<= 1024 CTAs)
                                 (size_t)n * sizeof(double),               // d
                                 (size_t)n * sizeof(double),               // e (= beta)
                                 (size_t)n * sizeof(double),               // lam (Rayleigh quotients)
@@ -895,7 +900,6 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   float2* pbuf = reinterpret_cast<float2*>(w + P.off[1]);
   float2* rowbuf = reinterpret_cast<float2*>(w + P.off[2]);
   float* part = reinterpret_cast<float*>(w + P.off[3]);
-  unsigned* flags = reinterpret_cast<unsigned*>(part + 2 * 1024);
   double* d = reinterpret_cast<double*>(w + P.off[4]);
   double* e = reinterpret_cast<double*>(w + P.off[5]);
   double* lam = reinterpret_cast<double*>(w + P.off[6]);
@@ -907,7 +911,6 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   double* Z = reinterpret_cast<double*>(w + P.off[12]);
   cudaError_t e_ = cudaMemsetAsync(ctl, 0, sizeof(HeCtl), st);
   if (e_ != cudaSuccess) return e_;
-  if ((e_ = cudaMemsetAsync(flags, 0, 1024 * sizeof(unsigned), st)) != cudaSuccess) return e_;
   float2* S = reinterpret_cast<float2*>(H);
   gram_scale_kernel<<<1, 1024, 0, st>>>(S, n, ctl);
   if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
@@ -930,11 +933,10 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   int per_sm = 0;
   if ((e_ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, TD_THREADS, dsm)) != cudaSuccess) return e_;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (!smem_rows) G = std::min(sms * per_sm, std::min(TD_THREADS, std::max(1, n / 8)));
-  if (G > TD_THREADS) return cudaErrorInvalidConfiguration;   // one barrier flag per thread
+  if (!smem_rows) G = std::min(sms * per_sm, std::min(1024, std::max(1, n / 8)));
   {
     int nn = n;
-    void* args[] = {&S, &nn, &d, &e, &tau, &pbuf, &rowbuf, &part, &flags, &ctl};
+    void* args[] = {&S, &nn, &d, &e, &tau, &pbuf, &rowbuf, &part, &ctl};
     e_ = cudaLaunchCooperativeKernel(tfn, dim3(G), dim3(TD_THREADS), args, dsm, st);
     if (e_ != cudaSuccess) return e_;
   }
@@ -953,9 +955,10 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
     const size_t ism = per_thread * iv;
     if ((e_ = allow_dyn_smem((const void*)tri_invit_kernel)) != cudaSuccess) return e_;
     const int kv = kk > chi ? chi : kk;   // vectors the truncation can keep
-    tri_invit_kernel<<<(kk + iv - 1) / iv, iv, ism, st>>>(d, e, n, kk, kv, lam32, resolve, Z, lam, ctl);
+    const double cut2 = cut * cut;
+    tri_invit_kernel<<<(kk + iv - 1) / iv, iv, ism, st>>>(d, e, n, kk, kv, lam32, cut2, resolve, Z, lam, ctl);
     if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
-    tri_cluster_kernel<<<kv, 256, 0, st>>>(d, e, n, kk, kv, lam32, 3e-5, Z, lam, ctl);
+    tri_cluster_kernel<<<kv, 256, 0, st>>>(d, e, n, kk, kv, lam32, cut2, 3e-5, Z, lam, ctl);
     if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
   }
   TruncResult* tr = reinterpret_cast<TruncResult*>(res);

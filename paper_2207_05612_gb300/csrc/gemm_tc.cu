@@ -508,13 +508,21 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
   a.alpha_re = (float)g.alpha_re; a.alpha_im = (float)g.alpha_im;
   a.err = err_dev;
   const long long tiles = (long long)((2 * g.N + TC_BN - 1) / TC_BN) * ((g.M + TC_BM - 1) / TC_BM) * g.b1 * g.b2;
+  // split-K for grids of a few waves: one CTA per SM is resident (the ring
+  // takes 192 KB of shared memory), so a grid of T tiles split s ways runs
+  // ceil(T s / SMs) waves of K / s blocks each; take the s (<= 32, >= 4 K
+  // blocks per split) with the fewest wave-blocks, preferring the smaller s
+  // within 3% (each split adds a partial product to write and sum)
   int split = 1;
-  const long long want = 2LL * sm_count();
-  if (tiles < want && a.ktiles >= 8) {
-    split = (int)((want + tiles - 1) / tiles);
-    if (split > a.ktiles / 4) split = a.ktiles / 4;
-    if (split > 32) split = 32;
-    if (split < 1) split = 1;
+  const long long sms = sm_count();
+  if (tiles < 4 * sms && a.ktiles >= 8) {
+    double best = 1e300;
+    const int smax = std::min(32, a.ktiles / 4);
+    for (int sp = 1; sp <= smax; ++sp) {
+      const long long waves = (tiles * sp + sms - 1) / sms;
+      const double cost = (double)waves * (double)((a.ktiles + sp - 1) / sp);
+      if (cost < 0.97 * best) { best = cost; split = sp; }
+    }
   }
   if ((long long)g.b1 * g.b2 * split > 65535) split = 1;
   a.per = (a.ktiles + split - 1) / split;
