@@ -275,6 +275,7 @@ dmrgc_status eig_try(dmrgc_ctx* c, int bond, const void* G, int rows, int kdim, 
     g.B = G; g.ldb = rows; g.opB = OP_N;
   }
   g.C = c->jw.p; g.ldc = rows;
+  g.upper_only = 1;   // Hermitian: the eigensolver mirrors the upper triangle
   const int gp = c->opt.precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3;
   TRY(gemm(c, g, gp));
   const int kk = std::min(c->chi + 1, rows);
@@ -1941,6 +1942,7 @@ dmrgc_status dmrgc_test_svd_gram(int precision, int m, int n, const double* G, i
   g.A = dG; g.lda = m; g.opA = OP_T;
   g.B = dG; g.ldb = m; g.opB = OP_R;
   g.C = dH; g.ldc = m;
+  g.upper_only = 1;
   TcWork w;
   cudaError_t e = run_gemm(precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3, g, &w, err, 0);
   if (e == cudaSuccess) e = eig_truncate(dH, m, chi, rel_cut, 0.0, kEigResolve, work, res, dU, 0, 0, nullptr);

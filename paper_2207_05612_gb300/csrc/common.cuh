@@ -45,6 +45,8 @@ struct GemmArgs {
   void* C = nullptr; long long ldc = 0, sC1 = 0, sC2 = 0;
   double alpha_re = 1.0, alpha_im = 0.0;
   int beta_one = 0;   // 1: accumulate into C
+  int upper_only = 0; // 1 (M == N, one instance, tensor-core path): only the output tiles that
+                      // touch the upper triangle are computed; C below them is left undefined
 };
 
 cudaError_t gemm_simt(const GemmArgs& g, bool fp64, cudaStream_t st);

@@ -46,9 +46,9 @@ namespace {
 
 struct HeCtl {
   int err;            // 0 ok, DMRGC_ETIMEOUT
-  unsigned count;
-  unsigned gen;
-  int status;         // tri_invit: 0 ok, 1 cluster too large
+  unsigned count;     // grid-barrier arrivals of the tridiagonalisation (never reset in a launch)
+  unsigned gen;       // (unused)
+  int status;         // inverse iteration / clusters: 0 ok, 1 not resolved
   float scale;        // max(|d|, |beta|) of T, for the tridiagonal kernels
   int pad0;
   double gscale;      // max_i H_ii: H was divided by it
@@ -58,33 +58,35 @@ static_assert(sizeof(HeCtl) == 64, "control block layout");
 
 constexpr unsigned long long kHeSpinLimit = 20000000ull;   // x ~64 ns, about 1.3 s
 
-__device__ __forceinline__ bool he_grid_barrier(HeCtl* c, unsigned nblocks) {
+// Grid barrier: every CTA adds 1 to a counter that is never reset (zeroed
+// before the launch) and waits until it reaches `target` = the number of
+// arrivals of all steps so far, so no CTA has to observe a second write after
+// the last arrival (bounded; on timeout or another CTA's error every thread
+// of the CTA returns false).
+__device__ __forceinline__ bool he_grid_barrier(HeCtl* c, unsigned target) {
+  __shared__ int s_bad;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &c->gen;
+    volatile unsigned* vcount = &c->count;
     volatile int* verr = &c->err;
-    const unsigned g = *vgen;
+    int bad = 0;
     __threadfence();
-    const unsigned arrived = atomicAdd(&c->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&c->count, 0u);
-      __threadfence();
-      atomicAdd(&c->gen, 1u);
-    } else {
-      unsigned long long it = 0;
-      while (*vgen == g) {
-        if (it > 2048) __nanosleep(32);
-        if (*verr != 0) break;
-        if (++it > kHeSpinLimit) {
-          atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
-          break;
-        }
+    atomicAdd(&c->count, 1u);
+    unsigned long long it = 0;
+    while (*vcount < target) {
+      if (it > 2048) __nanosleep(32);
+      if (*verr != 0) { bad = 1; break; }
+      if (++it > kHeSpinLimit) {
+        atomicExch(&c->err, (int)DMRGC_ETIMEOUT);
+        bad = 1;
+        break;
       }
     }
     __threadfence();
+    s_bad = bad;
   }
   __syncthreads();
-  return *((volatile int*)&c->err) == 0;
+  return s_bad == 0;
 }
 
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
@@ -100,6 +102,20 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+// block sum with one barrier: the caller alternates `red` buffers so that a
+// buffer is rewritten only after a barrier has passed since its last read
+template <int NT>
+__device__ __forceinline__ float block_sum1(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   float s = 0.f;
 #pragma unroll
@@ -123,19 +139,24 @@ __global__ void gram_scale_kernel(const float2* __restrict__ H, int n, HeCtl* ct
   }
 }
 
-// H <- (H + H^+) / (2 gscale): the Gram from the contraction engine is
-// Hermitian only to rounding (its two triangles are separate sums)
+// H <- upper triangle of H / gscale, mirrored: H[c][r] = conj(H[r][c]) for
+// c > r and a real diagonal (the contraction engine computes only the tiles
+// that touch the upper triangle of the Hermitian Gram)
 __global__ void herm_sym_kernel(float2* __restrict__ H, int n, const HeCtl* __restrict__ ctl) {
-  const float inv = (float)(0.5 / ctl->gscale);
+  const float inv = (float)(1.0 / ctl->gscale);
   const long long total = (long long)n * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / n), c = (int)(e % n);
     if (c < r) continue;
-    const float2 a = H[(long long)r * n + c], b = H[(long long)c * n + r];
-    const float2 m = make_float2(inv * (a.x + b.x), inv * (a.y - b.y));
-    H[(long long)r * n + c] = m;
-    H[(long long)c * n + r] = make_float2(m.x, -m.y);
+    const float2 a = H[(long long)r * n + c];
+    if (c == r) {
+      H[(long long)r * n + c] = make_float2(inv * a.x, 0.f);
+    } else {
+      const float2 m = make_float2(inv * a.x, inv * a.y);
+      H[(long long)r * n + c] = m;
+      H[(long long)c * n + r] = make_float2(m.x, -m.y);
+    }
   }
 }
 
@@ -187,6 +208,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
   float2* wp = sm + 2 * n;       // w of the previous step
   float2* rows = sm + 3 * n;     // owned rows (SMEM_ROWS)
   __shared__ float red[TD_THREADS / 32];
+  __shared__ float red2[TD_THREADS / 32];
   __shared__ float2 s_tau;
   __shared__ float s_k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -219,16 +241,16 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
       pv[q] = (pending && c < n) ? __ldcg(Pp + c) : make_float2(0.f, 0.f);
       rv[q] = c < n ? __ldcg(rj + c) : make_float2(0.f, 0.f);
     }
+    // w_{j-1} = p_{j-1} - K u_{j-1}, K = half the sum of the CTAs' partials,
+    // summed by every warp (no broadcast barrier); each thread writes w for
+    // its own columns and forms w_j of column j itself
+    float2 wj = make_float2(0.f, 0.f);
     if (pending) {
-      if (warp == 0) {
-        float v = 0.f;
-        for (int g = lane; g < G; g += 32) v += __ldcg(part + (size_t)((j - 1) & 1) * G + g);
+      float v = 0.f;
+      for (int g = lane; g < G; g += 32) v += __ldcg(part + (size_t)((j - 1) & 1) * G + g);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_k = 0.5f * v;
-      }
-      __syncthreads();
-      const float K = s_k;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const float K = 0.5f * v;
 #pragma unroll
       for (int q = 0; q < TD_NQ; ++q) {
         const int c = j + tid + TD_THREADS * q;
@@ -238,7 +260,8 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
           if (cta == 0) S[(size_t)(j - 1) * n + c] = u;   // reflector j-1 for the back-transformation
         }
       }
-      __syncthreads();
+      const float2 pj = tid == 0 ? pv[0] : __ldcg(Pp + j);
+      wj = make_float2(pj.x - K * up[j].x, pj.y - K * up[j].y);
     }
     // column j below the diagonal = conj(row j) right of it, with update j-1
     float ss = 0.f;
@@ -250,7 +273,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
       float2 s = rv[q];
       if (pending) {
         const float2 t1 = f2mul(up[j], f2conj(wp[c]));
-        const float2 t2 = f2mul(wp[j], f2conj(up[c]));
+        const float2 t2 = f2mul(wj, f2conj(up[c]));
         s.x -= t1.x + t2.x;
         s.y -= t1.y + t2.y;
       }
@@ -258,7 +281,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
       uc[c] = x;
       if (c > j + 1) ss += x.x * x.x + x.y * x.y;
     }
-    const float rest = block_sum<TD_THREADS>(ss, red);   // ends after a __syncthreads
+    const float rest = block_sum1<TD_THREADS>(ss, red);   // ends after a __syncthreads
     if (tid == 0) {
       float2 t, u0;
       float b;
@@ -267,7 +290,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
       uc[j] = make_float2(0.f, 0.f);
       s_tau = t;
       if (cta == 0) {
-        if (pending) djj.x -= 2.f * f2mul(up[j], f2conj(wp[j])).x;
+        if (pending) djj.x -= 2.f * f2mul(up[j], f2conj(wj)).x;
         d[j] = (double)djj.x;
         beta[j] = (double)b;
         tau[j] = t;
@@ -310,9 +333,9 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
         dot += f2cmul(tj, f2cmul(uc[r], p)).x;   // Re(conj(tau) conj(u_r) p_r)
       }
     }
-    const float tot = block_sum<TD_THREADS>(dot, red);
+    const float tot = block_sum1<TD_THREADS>(dot, red2);
     if (tid == 0) part[(size_t)(j & 1) * G + cta] = tot;
-    if (!he_grid_barrier(ctl, (unsigned)G)) return;
+    if (!he_grid_barrier(ctl, (unsigned)G * (unsigned)(j + 1))) return;
   }
   // trailing 2 x 2 block with the last pending update, and the 1 x 1 reflector
   // that makes its off-diagonal real (CTA 0)
@@ -762,11 +785,22 @@ __global__ void __launch_bounds__(256) bt_wy_kernel(const float2* __restrict__ S
 // mode 2: out[v * n + r] = conj(y_r).
 constexpr int BT_WARPS = 4;
 
-template <int E>
+// 8-byte asynchronous global -> shared copy; src_bytes 0 writes zeros
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// DB: the WY blocks are staged in two shared buffers, the next block's copy
+// in flight while the current one is applied (E <= 32: 2 x 64 KB)
+template <int E, bool DB>
 __global__ void __launch_bounds__(BT_WARPS * 32)
     he_backtrans_kernel(const float2* __restrict__ S, const float2* __restrict__ Tw, const double* __restrict__ Z,
                         int n, int kk, const TruncResult* __restrict__ res, int mode, float2* __restrict__ out) {
-  extern __shared__ float2 vsh[];   // WY columns x 32 E rows
+  extern __shared__ float2 vsh_all[];   // (DB ? 2 : 1) x WY columns x 32 E rows
   __shared__ float2 tsh[WY * WY];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = blockIdx.x * BT_WARPS + warp;
@@ -781,16 +815,32 @@ __global__ void __launch_bounds__(BT_WARPS * 32)
   }
   const int nref = n - 1;
   const int nblk = (nref + WY - 1) / WY;
-  for (int b = nblk - 1; b >= 0; --b) {
+  // V of block b (column i = u_{b WY + i}, zero at rows <= b WY + i) into buf
+  auto stage = [&](int b, float2* buf) {
     const int a = b * WY;
     const int m = min(WY, nref - a);
-    __syncthreads();
-    // stage V (column i = u_{a+i}, zero at rows <= a+i) and Tb
     for (int p = threadIdx.x; p < WY * 32 * E; p += BT_WARPS * 32) {
       const int i = p / (32 * E), r = p % (32 * E);
-      float2 val = make_float2(0.f, 0.f);
-      if (i < m && r > a + i && r < n) val = S[(size_t)(a + i) * n + r];
-      vsh[p] = val;
+      const bool ok = i < m && r > a + i && r < n;
+      if (DB) cp_async8(buf + p, ok ? S + (size_t)(a + i) * n + r : S, ok ? 8 : 0);
+      else buf[p] = ok ? S[(size_t)(a + i) * n + r] : make_float2(0.f, 0.f);
+    }
+    if (DB) cp_async_commit();
+  };
+  if (DB) stage(nblk - 1, vsh_all);
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int a = b * WY;
+    float2* vsh = DB ? vsh_all + (size_t)((nblk - 1 - b) & 1) * WY * 32 * E : vsh_all;
+    __syncthreads();   // every warp is done with the buffer about to be refilled, and with tsh
+    if (DB) {
+      if (b > 0) {
+        stage(b - 1, vsh_all + (size_t)((nblk - b) & 1) * WY * 32 * E);
+        cp_async_wait<1>();   // block b's copy has landed (b - 1's may still be in flight)
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      stage(b, vsh);
     }
     for (int p = threadIdx.x; p < WY * WY; p += BT_WARPS * 32) tsh[p] = Tw[(size_t)b * WY * WY + p];
     __syncthreads();
@@ -970,11 +1020,11 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
   if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
   const void* fn;
   int E;
-  if (n <= 32 * 8) { fn = (const void*)he_backtrans_kernel<8>; E = 8; }
-  else if (n <= 32 * 16) { fn = (const void*)he_backtrans_kernel<16>; E = 16; }
-  else if (n <= 32 * 32) { fn = (const void*)he_backtrans_kernel<32>; E = 32; }
-  else { fn = (const void*)he_backtrans_kernel<64>; E = 64; }
-  const size_t bsm = (size_t)WY * 32 * E * sizeof(float2);
+  if (n <= 32 * 8) { fn = (const void*)he_backtrans_kernel<8, true>; E = 8; }
+  else if (n <= 32 * 16) { fn = (const void*)he_backtrans_kernel<16, true>; E = 16; }
+  else if (n <= 32 * 32) { fn = (const void*)he_backtrans_kernel<32, true>; E = 32; }
+  else { fn = (const void*)he_backtrans_kernel<64, false>; E = 64; }
+  const size_t bsm = (size_t)(E <= 32 ? 2 : 1) * WY * 32 * E * sizeof(float2);
   if ((e_ = allow_dyn_smem(fn)) != cudaSuccess) return e_;
   {
     const float2* Sc = S;

@@ -12,12 +12,14 @@
 // A'B'^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the lo*lo term is below the
 // FP32 accumulation error).
 //
-// Kernel: one CTA of 4 warps per 128 x 256 tile of C' (128 x 128 complex),
-// the accumulator in 256 TMEM columns.  Warp 0 (one thread) streams the K
-// blocks of A_hi, A_lo, B_hi, B_lo with TMA (128-byte swizzle, K-major) into a
-// 2-stage ring; warp 1 (one thread) issues 3 x (BK / MMA_K) MMAs per stage and
-// frees the stage with tcgen05.commit; all 4 warps then read TMEM
-// (32 lanes x 32 columns per load) and write complex C.  With split-K each
+// Kernel: persistent, one CTA of 6 warps per SM looping over 128 x 256 tiles
+// of C' (128 x 128 complex).  Warp 0 (one thread) streams the K blocks of
+// A_hi, A_lo, B_hi, B_lo with TMA (128-byte swizzle, K-major) into a 2-stage
+// ring; warp 1 (one thread) issues 3 x (BK / MMA_K) MMAs per stage into one of
+// two accumulators of 256 TMEM columns and frees the stage with
+// tcgen05.commit; warps 2-5 read the other accumulator (32 lanes x 32 columns
+// per load, each warp its quarter of the TMEM lanes) and write complex C, so
+// a tile's epilogue overlaps the next tile's main loop.  With split-K each
 // split writes its partial product to a workspace and one more kernel sums the
 // partials in a fixed order (no atomics), so every product is reproducible.
 // Every mbarrier wait is bounded by the global timer; an exhausted wait sets
@@ -35,7 +37,7 @@
 namespace dmrgc {
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_THREADS = 128, TC_STAGES = 2;
+constexpr int TC_BM = 128, TC_BN = 256, TC_THREADS = 192, TC_STAGES = 2, TC_ACC = 2;
 constexpr int TC_ROW_BYTES = 128;                        // one swizzle row of K per stage
 constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES;         // 16 KiB
 constexpr int TC_B_BYTES = TC_BN * TC_ROW_BYTES;         // 32 KiB
@@ -45,6 +47,8 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
   int M, N;            // complex output rows / cols
+  int tiles_n, tiles_m;   // tile grid of one instance and split; tiles run in the order (z, m, n)
+  long long total;        // tiles_n * tiles_m * batches * split
   int ktiles;          // K blocks of BK real elements
   int split;           // split-K factor
   int per;             // K blocks per split
@@ -54,6 +58,7 @@ struct TcArgs {
   long long ldc, sC1, sC2;
   float alpha_re, alpha_im;
   int mode;            // 0 store, 1 add to C (beta = 1), 2 split-K partial into P
+  int upper;           // 1: skip the tiles strictly below the diagonal (square C)
   float2* P;           // split-K partials [split][batch][M][N] (mode 2)
   int* err;
 };
@@ -173,32 +178,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accf = empty + TC_STAGES;      // accumulator a holds a finished tile (MMA -> epilogue)
+  uint64_t* acce = accf + TC_ACC;          // accumulator a has been read out (epilogue -> MMA)
+  uint64_t* drain = acce + TC_ACC;         // every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* s_issued = reinterpret_cast<int*>(tmem_slot + 2);   // loads issued / stages consumed (teardown)
+  int* s_consumed = s_issued + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = blockIdx.z;
-  const int batch = z / g.split, ks = z % g.split;
-  const int i1 = batch / g.b2, i2 = batch % g.b2;
-  const int instA = i1 * g.a_m1 + i2 * g.a_m2;
-  const int instB = i1 * g.b_m1 + i2 * g.b_m2;
-  const int m0 = blockIdx.y * TC_BM;
-  const int n0 = blockIdx.x * TC_BN;            // in real columns of C' (= rows of B')
-  const int kt0 = ks * g.per;
-  int nk = g.ktiles - kt0;
-  if (nk > g.per) nk = g.per;
-  if (nk < 0) nk = 0;
+  const long long per_z = (long long)g.tiles_n * g.tiles_m;
+  // tile t -> (z = batch * split + ks, m tile, n tile); tiles strictly below
+  // the diagonal of a Hermitian product are skipped by every role alike
+  auto decode = [&](long long t, int& bx, int& by, int& z) {
+    z = (int)(t / per_z);
+    const long long r = t % per_z;
+    by = (int)(r / g.tiles_n);
+    bx = (int)(r % g.tiles_n);
+  };
+  auto kblocks = [&](int ks) {
+    int nk = g.ktiles - ks * g.per;
+    if (nk > g.per) nk = g.per;
+    return nk < 0 ? 0 : nk;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int a = 0; a < TC_ACC; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], 4); }
+    mbar_init(drain, 1);
     *abort_flag = 0;
+    *s_issued = 0;
+    *s_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(256)
+                 "r"(TC_ACC * 256)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -207,30 +222,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int issued_loads = 0, issued_mma = 0;
-  if (nk > 0) {
-    if (warp == 0 && lane == 0) {
-      // ---- TMA producer
-      for (int it = 0; it < nk; ++it) {
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int it = 0;
+    for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
+      int bx, by, z;
+      decode(t, bx, by, z);
+      if (g.upper && by > bx) continue;
+      const int batch = z / g.split, ks = z % g.split;
+      const int i1 = batch / g.b2, i2 = batch % g.b2;
+      const int instA = i1 * g.a_m1 + i2 * g.a_m2, instB = i1 * g.b_m1 + i2 * g.b_m2;
+      const int nk = kblocks(ks), kt0 = ks * g.per;
+      for (int k = 0; k < nk; ++k, ++it) {
         const int s = it % TC_STAGES;
         const uint32_t ph = (uint32_t)((it / TC_STAGES) & 1);
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { *abort_flag = 1; break; }
         uint8_t* st = smem + s * TC_STAGE_BYTES;
         mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-        const int kx = (kt0 + it) * BK;
-        tma_load_3d(st, &tA_hi, kx, m0, instA, &full[s]);
-        tma_load_3d(st + TC_A_BYTES, &tA_lo, kx, m0, instA, &full[s]);
-        tma_load_3d(st + 2 * TC_A_BYTES, &tB_hi, kx, n0, instB, &full[s]);
-        tma_load_3d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tB_lo, kx, n0, instB, &full[s]);
-        ++issued_loads;
+        const int kx = (kt0 + k) * BK;
+        tma_load_3d(st, &tA_hi, kx, by * TC_BM, instA, &full[s]);
+        tma_load_3d(st + TC_A_BYTES, &tA_lo, kx, by * TC_BM, instA, &full[s]);
+        tma_load_3d(st + 2 * TC_A_BYTES, &tB_hi, kx, bx * TC_BN, instB, &full[s]);
+        tma_load_3d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tB_lo, kx, bx * TC_BN, instB, &full[s]);
+        *s_issued = it + 1;
       }
-    } else if (warp == 1 && lane == 0) {
-      // ---- MMA issuer
-      constexpr uint32_t ID = idesc<ESZ>(TC_BM, TC_BN);
-      for (int it = 0; it < nk; ++it) {
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t ID = idesc<ESZ>(TC_BM, TC_BN);
+    int it = 0, lt = 0;
+    for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
+      int bx, by, z;
+      decode(t, bx, by, z);
+      if (g.upper && by > bx) continue;
+      const int nk = kblocks(z % g.split);
+      const int a = lt & 1;
+      if (!mbar_wait(&acce[a], (uint32_t)(((lt >> 1) & 1) ^ 1), abort_flag)) { *abort_flag = 1; break; }
+      tc_fence_after();
+      const uint32_t acc_tmem = tmem + (uint32_t)(a * 256);
+      bool ok = true;
+      for (int k = 0; k < nk; ++k, ++it) {
         const int s = it % TC_STAGES;
         const uint32_t ph = (uint32_t)((it / TC_STAGES) & 1);
-        if (!mbar_wait(&full[s], ph, abort_flag)) { *abort_flag = 1; break; }
+        if (!mbar_wait(&full[s], ph, abort_flag)) { *abort_flag = 1; ok = false; break; }
         tc_fence_after();
         const uint32_t base = smem_u32(smem + s * TC_STAGE_BYTES);
         const uint64_t a_hi = sdesc_sw128(base), a_lo = sdesc_sw128(base + TC_A_BYTES);
@@ -239,73 +273,86 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int kk = 0; kk < KSTEPS; ++kk) {
           const uint64_t off = (uint64_t)((kk * MMA_K * ESZ) >> 4);   // 32 B per K step
-          umma<ESZ>(tmem, a_hi + off, b_hi + off, ID, (it | kk) ? 1u : 0u);
-          umma<ESZ>(tmem, a_hi + off, b_lo + off, ID, 1u);
-          umma<ESZ>(tmem, a_lo + off, b_hi + off, ID, 1u);
+          umma<ESZ>(acc_tmem, a_hi + off, b_hi + off, ID, (k | kk) ? 1u : 0u);
+          umma<ESZ>(acc_tmem, a_hi + off, b_lo + off, ID, 1u);
+          umma<ESZ>(acc_tmem, a_lo + off, b_hi + off, ID, 1u);
         }
         umma_commit(&empty[s]);
-        ++issued_mma;
+        *s_consumed = it + 1;
       }
-      umma_commit(done);   // arrives once every MMA issued above has completed
+      if (!ok) break;
+      umma_commit(&accf[a]);   // arrives once the tile's MMAs have completed
+      ++lt;
     }
-  }
-  __syncwarp();
-
-  // ---- epilogue: all four warps
-  bool ok = true;
-  if (nk > 0) ok = mbar_wait(done, 0, abort_flag);
-  if (!ok || *abort_flag) {
-    if (threadIdx.x == 0) atomicExch(g.err, (int)DMRGC_ETIMEOUT);
-  } else if (nk > 0) {
-    tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    float2* Cb = g.C + (long long)i1 * g.sC1 + (long long)i2 * g.sC2;
+  } else if (warp >= 2) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
+    const int q = warp & 3;
+    int lt = 0;
+    for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
+      int bx, by, z;
+      decode(t, bx, by, z);
+      if (g.upper && by > bx) continue;
+      const int a = lt & 1;
+      if (!mbar_wait(&accf[a], (uint32_t)((lt >> 1) & 1), abort_flag)) { *abort_flag = 1; break; }
+      tc_fence_after();
+      const int batch = z / g.split, ks = z % g.split;
+      const int i1 = batch / g.b2, i2 = batch % g.b2;
+      const int row = by * TC_BM + q * 32 + lane;
+      const int n0 = bx * TC_BN;
+      float2* Cb = g.C + (long long)i1 * g.sC1 + (long long)i2 * g.sC2;
 #pragma unroll 1
-    for (int c = 0; c < TC_BN / 32; ++c) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-      if (row < g.M) {
-        const int ncol0 = (n0 + c * 32) >> 1;
-        float2* dst = Cb + (long long)row * g.ldc + ncol0;
+      for (int c = 0; c < TC_BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 256 + c * 32), r);
+        if (row < g.M) {
+          const int ncol0 = (n0 + c * 32) >> 1;
+          float2* dst = Cb + (long long)row * g.ldc + ncol0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (ncol0 + j < g.N) {
-            const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
-            const float vr = re * g.alpha_re - im * g.alpha_im;
-            const float vi = re * g.alpha_im + im * g.alpha_re;
-            if (g.mode == 2) {
-              float2* pd = g.P + ((long long)ks * (gridDim.z / g.split) + batch) * ((long long)g.M * g.N) +
-                           (long long)row * g.N + ncol0;
-              pd[j] = make_float2(vr, vi);
-            } else if (g.mode == 1) {
-              float2 o = dst[j];
-              dst[j] = make_float2(o.x + vr, o.y + vi);
-            } else {
-              dst[j] = make_float2(vr, vi);
+          for (int j = 0; j < 16; ++j) {
+            if (ncol0 + j < g.N) {
+              const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
+              const float vr = re * g.alpha_re - im * g.alpha_im;
+              const float vi = re * g.alpha_im + im * g.alpha_re;
+              if (g.mode == 2) {
+                float2* pd = g.P + ((long long)ks * (g.b1 * g.b2) + batch) * ((long long)g.M * g.N) +
+                             (long long)row * g.N + ncol0;
+                pd[j] = make_float2(vr, vi);
+              } else if (g.mode == 1) {
+                float2 o = dst[j];
+                dst[j] = make_float2(o.x + vr, o.y + vi);
+              } else {
+                dst[j] = make_float2(vr, vi);
+              }
             }
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a])) : "memory");
+      ++lt;
     }
   }
+  __syncwarp();
   // ---- teardown: nothing may still write smem or TMEM when the CTA leaves
+  __syncthreads();
+  if (warp == 1 && lane == 0) {
+    volatile int never = 0;
+    umma_commit(drain);
+    mbar_wait(drain, 0, &never);   // every issued MMA has completed (bounded)
+  }
   if (*abort_flag && warp == 0 && lane == 0) {
-    // drain TMA loads whose stage the MMA thread never consumed (bounded)
+    // TMA loads the MMA thread never consumed (bounded waits)
     volatile int never = 0;
-    for (int it = 0; it < issued_loads; ++it) {
-      const int s = it % TC_STAGES;
-      mbar_wait(&full[s], (uint32_t)((it / TC_STAGES) & 1), &never);
-    }
+    for (int it = *s_consumed; it < *s_issued; ++it)
+      mbar_wait(&full[it % TC_STAGES], (uint32_t)((it / TC_STAGES) & 1), &never);
   }
-  if (*abort_flag && nk > 0) {
-    volatile int never = 0;
-    mbar_wait(done, 0, &never);   // every issued MMA has completed (bounded)
-  }
+  if (*abort_flag && threadIdx.x == 0) atomicExch(g.err, (int)DMRGC_ETIMEOUT);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_ACC * 256) : "memory");
   }
 }
 
@@ -507,7 +554,12 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
   a.C = (float2*)g.C; a.ldc = g.ldc; a.sC1 = g.sC1; a.sC2 = g.sC2;
   a.alpha_re = (float)g.alpha_re; a.alpha_im = (float)g.alpha_im;
   a.err = err_dev;
-  const long long tiles = (long long)((2 * g.N + TC_BN - 1) / TC_BN) * ((g.M + TC_BM - 1) / TC_BM) * g.b1 * g.b2;
+  long long tiles = (long long)((2 * g.N + TC_BN - 1) / TC_BN) * ((g.M + TC_BM - 1) / TC_BM) * g.b1 * g.b2;
+  const bool upper = g.upper_only && g.M == g.N && g.b1 * g.b2 == 1 && !g.beta_one;
+  if (upper) {   // tiles on or above the diagonal only
+    const long long tm = (g.M + TC_BM - 1) / TC_BM;
+    tiles = tm * (tm + 1) / 2;
+  }
   // split-K for grids of a few waves: one CTA per SM is resident (the ring
   // takes 192 KB of shared memory), so a grid of T tiles split s ways runs
   // ceil(T s / SMs) waves of K / s blocks each; take the s (<= 32, >= 4 K
@@ -529,6 +581,7 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
   split = (a.ktiles + a.per - 1) / a.per;   // every split owns at least one K block
   a.split = split;
   a.mode = split > 1 ? 2 : (g.beta_one ? 1 : 0);
+  a.upper = upper ? 1 : 0;
   const int nbatch = g.b1 * g.b2;
   if (split > 1) {
     if ((e = w.ensure(4, (size_t)split * nbatch * g.M * g.N * sizeof(float2))) != cudaSuccess) return e;
@@ -536,9 +589,11 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
   }
   if (launches) *launches = 3 + (split > 1 ? 1 : 0);
   if ((e = allow_dyn_smem((const void*)tc_gemm_kernel<ESZ>)) != cudaSuccess) return e;
-  dim3 grid((2 * g.N + TC_BN - 1) / TC_BN, (g.M + TC_BM - 1) / TC_BM, (unsigned)(nbatch * split));
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  tc_gemm_kernel<ESZ><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(tAh, tAl, tBh, tBl, a);
+  a.tiles_n = (2 * g.N + TC_BN - 1) / TC_BN;
+  a.tiles_m = (g.M + TC_BM - 1) / TC_BM;
+  a.total = (long long)a.tiles_n * a.tiles_m * nbatch * split;
+  const long long ctas = std::min<long long>(a.total, (long long)sm_count());
+  tc_gemm_kernel<ESZ><<<(unsigned)ctas, TC_THREADS, TC_SMEM_BYTES, st>>>(tAh, tAl, tBh, tBl, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (split > 1) {
     const long long mn = (long long)g.M * g.N;

@@ -4,6 +4,7 @@ single kernel.
 
   python -m paper_2207_05612_gb300.microbench gemm --precision bf16x3 --m 65536 --n 1024 --k 512
   python -m paper_2207_05612_gb300.microbench svd --precision fp32 --m 1024 --n 1024 [--jacobi gram]
+  python -m paper_2207_05612_gb300.microbench gram --precision tf32x3 --m 1024 --n 1024
 
 gemm: C = A B through dmrgc_test_gemm (host complex128 buffers in and out, so
 the wall time includes the transfers and the operand split); reports the wall
@@ -12,6 +13,11 @@ svd: the one-sided Jacobi, truncation and gather on a device matrix through
 dmrgc_svd_noalloc, timed with CUDA events on its stream; the matrix is
 re-copied from a pristine device copy before each call (the copy is outside
 the events).
+gram: the Gram-eigensolver truncated SVD (chi = m / 2) through
+dmrgc_test_svd_gram (host buffers in and out): the Gram product, the
+tridiagonalisation, bisection, inverse iteration, the cluster pass and the
+back-transformation, one launch each per call; reports the wall time per call
+and the largest error of the kept singular values against LAPACK.
 """
 from __future__ import annotations
 
@@ -83,9 +89,24 @@ def bench_svd(prec: int, m: int, n: int, reps: int, seed: int) -> dict:
             "max_rel_err_s": err}
 
 
+def bench_gram(prec: int, m: int, n: int, reps: int, seed: int) -> dict:
+    rng = np.random.default_rng(seed)
+    g = _cplx(rng, (m, n)) / np.sqrt(m)
+    chi = min(m, n) // 2
+    binding.dmrgc_test_svd_gram(prec, g, chi, 2e-5)   # warm-up
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s, k, _ = binding.dmrgc_test_svd_gram(prec, g, chi, 2e-5)
+    dt = (time.perf_counter() - t0) / reps
+    ref = np.linalg.svd(g, compute_uv=False)
+    err = float(np.abs(s[:chi] - ref[:chi]).max() / ref[0])
+    return {"kernel": "gram", "m": m, "n": n, "chi": chi, "k": k, "wall_ms_per_call": dt * 1e3,
+            "max_rel_err_kept_s": err, "note": "wall time includes host<->device copies"}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["gemm", "svd"])
+    ap.add_argument("kernel", choices=["gemm", "svd", "gram"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--m", type=int, default=1024)
     ap.add_argument("--n", type=int, default=1024)
@@ -99,6 +120,8 @@ def main(argv=None) -> int:
     prec = PREC[a.precision]
     if a.kernel == "gemm":
         out = bench_gemm(prec, a.m, a.n, a.k, a.reps, a.seed)
+    elif a.kernel == "gram":
+        out = bench_gram(prec, a.m, a.n, a.reps, a.seed)
     else:
         out = bench_svd(prec, a.m, a.n, a.reps, a.seed)
     out["precision"] = a.precision
