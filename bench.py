@@ -43,9 +43,9 @@ DTYPE_NAME = {"fp64": "c128-f64", "bf16x3": "c64-bf16x3", "tf32x3": "c64-tf32x3"
 # ncu capture of each kernel at the shape that dominates the bench (summaries
 # in profiles/).  Only reported while the bench runs that kernel variant.
 NCU_TRAFFIC = {
-    "jacobi_wp4": {"bytes": 10.49e6, "launch": "1024 x 1024 complex64 (saturated bond, chi = 512)",
+    "jacobi_wp4": {"bytes": 10.91e6, "launch": "1024 x 1024 complex64 (saturated bond, chi = 512)",
                    "profile": "profiles/jacobi_wp4_1024x1024_fp32.md"},
-    "tc_gemm_bf16x3": {"bytes": 760.07e6, "launch": "M 65536, N 1024, K 512",
+    "tc_gemm_bf16x3": {"bytes": 761.73e6, "launch": "M 65536, N 1024, K 512",
                        "profile": "profiles/tc_gemm_65536x1024x512_bf16x3.md"},
 }
 FP32_LANES_PER_SM = 128

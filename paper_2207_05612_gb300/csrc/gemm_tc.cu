@@ -188,9 +188,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long per_z = (long long)g.tiles_n * g.tiles_m;
-  // tile t -> (z = batch * split + ks, m tile, n tile); tiles strictly below
-  // the diagonal of a Hermitian product are skipped by every role alike
+  // tile t -> (z = batch * split + ks, m tile, n tile); a Hermitian product
+  // enumerates only the tiles on or above the diagonal (bx >= by), row by row
   auto decode = [&](long long t, int& bx, int& by, int& z) {
+    if (g.upper) {
+      const long long per_u = (long long)g.tiles_m * (g.tiles_m + 1) / 2;
+      z = (int)(t / per_u);
+      int r = (int)(t % per_u);
+      by = 0;
+      while (r >= g.tiles_m - by) { r -= g.tiles_m - by; ++by; }
+      bx = by + r;
+      return;
+    }
     z = (int)(t / per_z);
     const long long r = t % per_z;
     by = (int)(r / g.tiles_n);
@@ -228,7 +237,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
       int bx, by, z;
       decode(t, bx, by, z);
-      if (g.upper && by > bx) continue;
       const int batch = z / g.split, ks = z % g.split;
       const int i1 = batch / g.b2, i2 = batch % g.b2;
       const int instA = i1 * g.a_m1 + i2 * g.a_m2, instB = i1 * g.b_m1 + i2 * g.b_m2;
@@ -254,7 +262,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
       int bx, by, z;
       decode(t, bx, by, z);
-      if (g.upper && by > bx) continue;
       const int nk = kblocks(z % g.split);
       const int a = lt & 1;
       if (!mbar_wait(&acce[a], (uint32_t)(((lt >> 1) & 1) ^ 1), abort_flag)) { *abort_flag = 1; break; }
@@ -291,7 +298,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (long long t = blockIdx.x; t < g.total && !*abort_flag; t += gridDim.x) {
       int bx, by, z;
       decode(t, bx, by, z);
-      if (g.upper && by > bx) continue;
       const int a = lt & 1;
       if (!mbar_wait(&accf[a], (uint32_t)((lt >> 1) & 1), abort_flag)) { *abort_flag = 1; break; }
       tc_fence_after();
@@ -591,7 +597,8 @@ cudaError_t run_tc(const GemmArgs& g, TcWork& w, int* err_dev, cudaStream_t st, 
   if ((e = allow_dyn_smem((const void*)tc_gemm_kernel<ESZ>)) != cudaSuccess) return e;
   a.tiles_n = (2 * g.N + TC_BN - 1) / TC_BN;
   a.tiles_m = (g.M + TC_BM - 1) / TC_BM;
-  a.total = (long long)a.tiles_n * a.tiles_m * nbatch * split;
+  a.total = (upper ? (long long)a.tiles_m * (a.tiles_m + 1) / 2 : (long long)a.tiles_n * a.tiles_m) *
+            nbatch * split;
   const long long ctas = std::min<long long>(a.total, (long long)sm_count());
   tc_gemm_kernel<ESZ><<<(unsigned)ctas, TC_THREADS, TC_SMEM_BYTES, st>>>(tAh, tAl, tBh, tBl, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
