@@ -441,6 +441,9 @@ def main(argv=None):
     ap.add_argument("--batch-count", type=int, default=32, help="batch: number of instances")
     ap.add_argument("--workers", default="auto",
                     help="batch: worker streams, or 'auto' to pick the best of 1, 2, 4, 8, 16 on a calibration subset")
+    ap.add_argument("--batch-serial", type=int, default=1,
+                    help="batch: 1 also runs the instances one at a time (twice) for the speedup and the "
+                         "run-to-run spread; 0 runs the batched pass only")
     ap.add_argument("--layers", type=int, default=4, help="QAOA levels")
     ap.add_argument("--samples", type=int, default=10000)
     ap.add_argument("--chi-oracle", type=int, default=64)
@@ -861,12 +864,14 @@ def batch_report(args):
     else:
         workers = int(args.workers)
     wall_b, ups_b, res_b = run(insts, workers)
-    wall_s, ups_s, res_s = run(insts, 1)
-    dlog = max(abs(a.log_F_tilde - b.log_F_tilde) for a, b in zip(res_b, res_s))
-    # run-to-run spread of the serial runs alone: split-K accumulation order is
-    # not fixed in the tensor-core modes, and truncated runs amplify it
-    _, _, res_s2 = run(insts, 1)
-    dlog_rep = max(abs(a.log_F_tilde - b.log_F_tilde) for a, b in zip(res_s, res_s2))
+    wall_s = ups_s = dlog = dlog_rep = None
+    if args.batch_serial:
+        wall_s, ups_s, res_s = run(insts, 1)
+        dlog = max(abs(a.log_F_tilde - b.log_F_tilde) for a, b in zip(res_b, res_s))
+        # run-to-run spread of the serial runs alone (0 when every reduction
+        # order is fixed)
+        _, _, res_s2 = run(insts, 1)
+        dlog_rep = max(abs(a.log_F_tilde - b.log_F_tilde) for a, b in zip(res_s, res_s2))
     print(json.dumps({
         "report": "batch", "precision": args.precision, "instances": len(insts),
         "workload": "random circuits, N in {16,20,24,30,36,42,54}, 8-20 cycles, chi in {32,64,128,256}, "
@@ -876,8 +881,8 @@ def batch_report(args):
         "updates": ups_b,
         "workers": workers, "autotune_updates_per_s": {str(k): v for k, v in tune.items()},
         "batched_updates_per_s": ups_b / wall_b, "batched_seconds": wall_b,
-        "serial_updates_per_s": ups_s / wall_s, "serial_seconds": wall_s,
-        "speedup": wall_s / wall_b,
+        "serial_updates_per_s": ups_s / wall_s if wall_s else None, "serial_seconds": wall_s,
+        "speedup": wall_s / wall_b if wall_s else None,
         "max_abs_dlog_F_tilde_batched_vs_serial": dlog,
         "max_abs_dlog_F_tilde_serial_vs_serial": dlog_rep,
         "log_F_tilde": [r.log_F_tilde for r in res_b]}))

@@ -168,7 +168,8 @@ dmrgc_status dmrgc_create(int n_qubits, const dmrgc_grid* grid, int chi,
  * after an update the tensor is replaced by the isometry spanning the same
  * space (left or right singular vectors; values at the numerical-zero level
  * dropped, so a bond can shrink).  1 <= group_sizes[tau] <= 20, summing to
- * n_qubits; EINVAL otherwise.  Amplitudes, sampling, overlaps and XEB are for
+ * n_qubits; EINVAL otherwise.  Amplitudes and Metropolis sampling read the
+ * grouped tensors directly; sequential sampling, overlaps and XEB are for
  * contexts with one qubit per tensor (dmrgc_create) and return EINVAL here;
  * dmrgc_get_mps returns the grouped tensors. */
 dmrgc_status dmrgc_create_grouped(int n_qubits, const dmrgc_grid* grid, const int* group_sizes, int n_groups,

@@ -1421,17 +1421,18 @@ int readout_precision(const dmrgc_ctx* c) {
   return c->opt.precision == DMRGC_FP32 ? DMRGC_FP32 : DMRGC_TF32X3;
 }
 
-int readout_chunk(const dmrgc_ctx* c, long long count, int maxb) {
-  const long long cap = (256ll << 20) / ((long long)2 * std::max(maxb, 1) * (long long)c->esz);
+// rows per chunk: W[B][phys r] stays within 256 MB (phys = 2 or 2^r_tau)
+int readout_chunk(const dmrgc_ctx* c, long long count, int maxb, long long phys = 2) {
+  const long long cap = (256ll << 20) / (phys * std::max(maxb, 1) * (long long)c->esz);
   return (int)std::max(1ll, std::min({count, cap, 16384ll}));
 }
 
-dmrgc_status readout_site(dmrgc_ctx* c, const void* Ai, int B, int l, int r) {
+dmrgc_status readout_site(dmrgc_ctx* c, const void* Ai, int B, int l, int r, int phys = 2) {
   GemmArgs g;   // W[b][(x c)] = sum_a V[b][a] A_i[a][(x c)]
-  g.M = B; g.N = 2 * r; g.K = l;
+  g.M = B; g.N = phys * r; g.K = l;
   g.A = c->rv[0].p; g.lda = l; g.opA = OP_N;
-  g.B = Ai; g.ldb = 2 * r; g.opB = OP_N;
-  g.C = c->rv[1].p; g.ldc = 2 * r;
+  g.B = Ai; g.ldb = (long long)phys * r; g.opB = OP_N;
+  g.C = c->rv[1].p; g.ldc = (long long)phys * r;
   return gemm(c, g, readout_precision(c));
 }
 
@@ -1445,10 +1446,16 @@ dmrgc_status amplitudes_device(dmrgc_ctx* c, const unsigned char* bits_dev, long
   std::vector<int>* bonds;
   auto& st = current_state(c, bonds);
   const int N = c->N;
-  const int maxb = *std::max_element(bonds->begin(), bonds->begin() + N + 1);
-  const int B0 = readout_chunk(c, count, maxb);
+  const int nt = c->ng > 0 ? c->ng : N;   // tensors; tensor i holds gsize[i] sites from gstart[i]
+  const int maxb = *std::max_element(bonds->begin(), bonds->begin() + nt + 1);
+  const int gmax = *std::max_element(c->gsize.begin(), c->gsize.begin() + nt);
+  const long long pmax = 1ll << gmax;
+  const int B0 = readout_chunk(c, count, maxb, pmax);
   TRY(ensure(c, c->rv[0], (size_t)B0 * maxb * c->esz));
-  TRY(ensure(c, c->rv[1], (size_t)B0 * 2 * maxb * c->esz));
+  TRY(ensure(c, c->rv[1], (size_t)B0 * pmax * maxb * c->esz));
+  TRY(ensure(c, c->order_d, sizeof(int) * N));   // qubit of each chain site
+  CK(cudaMemcpyAsync(c->order_d.p, c->order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
+  const int* od = (const int*)c->order_d.p;
   for (long long row0 = 0; row0 < count; row0 += B0) {
     const int B = (int)std::min<long long>(B0, count - row0);
     const unsigned char* bd = bits_dev + row0 * N;
@@ -1457,11 +1464,11 @@ dmrgc_status amplitudes_device(dmrgc_ctx* c, const unsigned char* bits_dev, long
       CK(readout_start(c->rv[0].p, B, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
-    for (int i = 0; i < N; ++i) {
-      const int l = (*bonds)[i], r = (*bonds)[i + 1];
-      TRY(readout_site(c, st[i].p, B, l, r));
+    for (int i = 0; i < nt; ++i) {
+      const int l = (*bonds)[i], r = (*bonds)[i + 1], g = c->gsize[i];
+      TRY(readout_site(c, st[i].p, B, l, r, 1 << g));
       Span sp(c, TC_OTHER);
-      CK(amp_select(c->rv[1].p, B, r, bd, N, c->order[i], c->rv[0].p, c->fp64, c->st));
+      CK(amp_select(c->rv[1].p, B, r, bd, N, od + c->gstart[i], g, c->rv[0].p, c->fp64, c->st));
       c->stats.kernel_launches++;
     }
     Span sp(c, TC_OTHER);
@@ -1477,7 +1484,6 @@ extern "C" {
 
 dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
   if (!c) return DMRGC_EINVAL;
-  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "amplitude: contexts with one qubit per tensor only");
   if (count < 0 || (count > 0 && (!bits || !out_re_im))) return fail(c, DMRGC_EINVAL, "bad amplitude arguments");
   if (count == 0) return DMRGC_OK;
   if (count > 0x7fffffffLL) return fail(c, DMRGC_EINVAL, "count too large");
@@ -1495,7 +1501,6 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
 dmrgc_status dmrgc_metropolis(dmrgc_ctx* c, int chains, int steps, unsigned long long seed, unsigned char* out_bits,
                               long long* accepted) {
   if (!c) return DMRGC_EINVAL;
-  if (c->ng > 0) return fail(c, DMRGC_EINVAL, "metropolis: contexts with one qubit per tensor only");
   if (chains < 1 || steps < 1 || !out_bits || (long long)chains * (steps + 1) > (1ll << 40))
     return fail(c, DMRGC_EINVAL, "bad metropolis arguments");
   const int N = c->N;

@@ -203,14 +203,15 @@ cudaError_t from_complex128(const double2* src, long long n, bool fp64, void* ds
 // whose running row vectors V[B][l] the caller multiplies by the site tensor
 // (W[B][2 r] = V A_i, the contraction engine) before each call:
 //  readout_start: V[b][0] = 1;
-//  amp_select:    V[b][c] = W[b][x_b r + c], x_b = bits[b * n + qubit];
+//  amp_select:    V[b][c] = W[b][x_b r + c], x_b = the bits of the tensor's g
+//                 qubits (qubits[0..g), the first the most significant), W[B][2^g r];
 //  sample_select: draws bit x of sample row0 + b at `site` from p_x = |W_x|^2
 //                 (T = null) or Re <T_x, W_x> (T = W E, left of the centre),
 //                 out[(row0 + b) * n + qubit] = x, V[b] = W_x / sqrt(p_x);
 //  amp_store:     out[b] = V[b][0] as complex128.
 cudaError_t readout_start(void* V, int B, bool fp64, cudaStream_t st);
-cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, int qubit, void* V, bool fp64,
-                       cudaStream_t st);
+cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, const int* qubits, int g,
+                       void* V, bool fp64, cudaStream_t st);
 cudaError_t sample_select(const void* W, const void* T, int B, int r, unsigned long long seed, long long row0, int n,
                           int site, int qubit, unsigned char* out, void* V, bool fp64, cudaStream_t st);
 cudaError_t amp_store(const void* V, int B, double2* out, bool fp64, cudaStream_t st);

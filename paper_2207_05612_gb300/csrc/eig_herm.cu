@@ -165,20 +165,24 @@ __global__ void herm_sym_kernel(float2* __restrict__ H, int n, const HeCtl* __re
 // Reflector of x = (alpha, x_2..) (the LAPACK zlarfg convention, written with
 // the unscaled u): beta = -sign(Re alpha) |x| real, u = (alpha - beta, x_2..),
 // tau = -1 / (beta conj(alpha - beta)); then P = I - tau u u^+ is unitary and
-// P^+ x = beta e_1.  No reflection (tau = 0, beta = alpha) when x_2.. = 0 and
-// alpha is real.  With P^+ A P = A - u w^+ - w u^+, p = tau A u,
-// K = Re(conj(tau) u^+ p) / 2 and w = p - K u.
+// P^+ x = beta e_1.  No reflection (tau = 0, beta = Re alpha) when x_2.. = 0
+// and alpha is real, or when |x| < 1e-12: the scaled H has entries <= 1, so
+// dropping such a column perturbs it far below its FP32 rounding, while its
+// tau (~ 1 / |x|^2, formed through |x|^3) would overflow FP32 below ~1e-13.
+// With P^+ A P = A - u w^+ - w u^+, p = tau A u, K = Re(conj(tau) u^+ p) / 2
+// and w = p - K u.
 constexpr int TD_THREADS = 256;
 constexpr int TD_NQ = 8;   // columns per thread in the per-step loads: n <= 2048
 
 __device__ __forceinline__ void reflector(float2 alpha, float rest, float2& tau, float& beta, float2& u0) {
-  if (rest == 0.f && alpha.y == 0.f) {
+  const float n2 = alpha.x * alpha.x + alpha.y * alpha.y + rest;
+  if ((rest == 0.f && alpha.y == 0.f) || n2 < 1e-24f) {   // NaN takes the other branch
     tau = make_float2(0.f, 0.f);
     beta = alpha.x;
     u0 = alpha;
     return;
   }
-  const float nrm = sqrtf(alpha.x * alpha.x + alpha.y * alpha.y + rest);
+  const float nrm = sqrtf(n2);
   beta = alpha.x >= 0.f ? -nrm : nrm;
   u0 = make_float2(alpha.x - beta, alpha.y);
   // tau = -1 / (beta conj(u0)) = -u0 / (beta |u0|^2)
@@ -232,8 +236,8 @@ __global__ void __launch_bounds__(TD_THREADS, 1)
     const bool pending = j > 0;
     const float2* rj = j == 0 ? S : rowbuf + (size_t)(j % 3) * n;
     const float2* Pp = pbuf + (size_t)((j - 1) & 1) * n;
-    // one round of L2 loads per step: the partial sums (warp 0), p_{j-1} and
-    // row j; thread tid owns columns c = j + tid + TD_THREADS q
+    // one round of L2 loads per step: p_{j-1} and row j; thread tid owns
+    // columns c = j + tid + TD_THREADS q
     float2 pv[TD_NQ], rv[TD_NQ];
 #pragma unroll
     for (int q = 0; q < TD_NQ; ++q) {
@@ -465,7 +469,7 @@ __global__ void tri_bisect_kernel(const float* __restrict__ d, const float* __re
 // orthonormalises each such cluster afterwards (their span is the cluster's
 // invariant subspace, which is all the truncation uses) and forms the
 // Rayleigh quotients.  Only vectors 0..kv-1 above the cut (lam[v] > cut2
-// lam[0], cut2 = the cut on s squared) are computed: kv is the most the
+// lam[0], cut2 = half the cut on s squared) are computed: kv is the most the
 // truncation can keep, and the extra eigenvalue and those below the cut keep
 // their bisection values.  A computed eigenvalue below half the resolution
 // level (lam[v] < 0.5 resolve lam[0]) cannot belong to a resolved
@@ -659,8 +663,8 @@ __global__ void __launch_bounds__(256) tri_cluster_kernel(const double* __restri
 // wait ran out.  One CTA of 1024.
 __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restrict__ lam, int n, int kk, int chi,
                                                          double cut, double tie_rel, double resolve,
-                                                         const double* __restrict__ d0, TruncResult* res,
-                                                         HeCtl* ctl) {
+                                                         const double* __restrict__ d0, const float* __restrict__ lam32,
+                                                         double cut2, TruncResult* res, HeCtl* ctl) {
   __shared__ double red[32];
   double* s = reinterpret_cast<double*>(res + 1);
   int* perm = reinterpret_cast<int*>(s + n);
@@ -705,6 +709,8 @@ __global__ void __launch_bounds__(1024) eig_trunc_kernel(const double* __restric
     // a count set by the cut is trusted only when the cut itself (cut^2 in
     // eigenvalue units) lies at or above the resolution level
     else if ((by_cut && cut * cut < resolve) || !(lam[k - 1] >= resolve * lam[0]) || !(lam[0] > 0.0)) st = 1;
+    // every kept vector must be one inverse iteration computed
+    else if (k > kk || !((double)lam32[k - 1] > cut2 * (double)lam32[0])) st = 1;
     res->k = k;
     res->n = n;
     res->status = st;
@@ -782,7 +788,8 @@ __global__ void __launch_bounds__(256) bt_wy_kernel(const float2* __restrict__ S
 // y <- (I - V Tb V^+) y: c = V^+ y (WY reductions in one pass), c <- Tb c,
 // y -= V c.  The block's columns are staged in shared memory by the CTA.
 // Output: mode 0: out[r * k + v] = y_r; mode 1: out[v * n + r] = y_r;
-// mode 2: out[v * n + r] = conj(y_r).
+// mode 2: out[v * n + r] = conj(y_r).  A vector with a non-finite entry sets
+// res->status = 2 (the caller then takes the Jacobi SVD).
 constexpr int BT_WARPS = 4;
 
 // 8-byte asynchronous global -> shared copy; src_bytes 0 writes zeros
@@ -799,7 +806,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <int E, bool DB>
 __global__ void __launch_bounds__(BT_WARPS * 32)
     he_backtrans_kernel(const float2* __restrict__ S, const float2* __restrict__ Tw, const double* __restrict__ Z,
-                        int n, int kk, const TruncResult* __restrict__ res, int mode, float2* __restrict__ out) {
+                        int n, int kk, TruncResult* __restrict__ res, int mode, float2* __restrict__ out) {
   extern __shared__ float2 vsh_all[];   // (DB ? 2 : 1) x WY columns x 32 E rows
   __shared__ float2 tsh[WY * WY];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -891,6 +898,10 @@ __global__ void __launch_bounds__(BT_WARPS * 32)
     }
   }
   if (!active) return;
+  bool finite = true;
+#pragma unroll
+  for (int e = 0; e < E; ++e) finite = finite && isfinite(y[e].x) && isfinite(y[e].y);
+  if (!__all_sync(0xffffffffu, finite) && lane == 0) atomicExch(&res->status, 2);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = lane + 32 * e;
@@ -1005,14 +1016,18 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
     const size_t ism = per_thread * iv;
     if ((e_ = allow_dyn_smem((const void*)tri_invit_kernel)) != cudaSuccess) return e_;
     const int kv = kk > chi ? chi : kk;   // vectors the truncation can keep
-    const double cut2 = cut * cut;
+    // vectors are computed down to half the squared cut: the truncation
+    // counts with the Rayleigh quotients, which differ from the bisection
+    // values by far less than that margin, so it never counts a vector that
+    // was not computed (eig_trunc_kernel checks this too)
+    const double cut2 = 0.5 * cut * cut;
     tri_invit_kernel<<<(kk + iv - 1) / iv, iv, ism, st>>>(d, e, n, kk, kv, lam32, cut2, resolve, Z, lam, ctl);
     if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
     tri_cluster_kernel<<<kv, 256, 0, st>>>(d, e, n, kk, kv, lam32, cut2, 3e-5, Z, lam, ctl);
     if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
   }
   TruncResult* tr = reinterpret_cast<TruncResult*>(res);
-  eig_trunc_kernel<<<1, 1024, 0, st>>>(lam, n, kk, chi, cut, tie_rel, resolve, d, tr, ctl);
+  eig_trunc_kernel<<<1, 1024, 0, st>>>(lam, n, kk, chi, cut, tie_rel, resolve, d, lam32, 0.5 * cut * cut, tr, ctl);
   if ((e_ = cudaGetLastError()) != cudaSuccess) return e_;
   // 3. back-transformation of the k kept eigenvectors
   const int nblk = (n - 1 + WY - 1) / WY;
@@ -1032,7 +1047,7 @@ cudaError_t eig_truncate(void* H, int n, int chi, double cut, double tie_rel, do
     const double* zc = Z;
     float2* o = reinterpret_cast<float2*>(out);
     int nn = n, kkk = kk, md = mode;
-    const TruncResult* rc = tr;
+    TruncResult* rc = tr;
     void* args[] = {(void*)&Sc, (void*)&tc, (void*)&zc, &nn, &kkk, (void*)&rc, &md, &o};
     e_ = cudaLaunchKernel(fn, dim3((kk + BT_WARPS - 1) / BT_WARPS), dim3(BT_WARPS * 32), args, bsm, st);
     if (e_ != cudaSuccess) return e_;

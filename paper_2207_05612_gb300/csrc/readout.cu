@@ -44,10 +44,11 @@ __device__ double block_sum(double v, double* red) {
 // amplitudes: V'[b][c] = W[b][x_b r + c], x_b the string's bit at site i
 template <typename C2>
 __global__ void amp_select_kernel(const C2* __restrict__ W, int r, const unsigned char* __restrict__ bits,
-                                  int n, int qubit, C2* __restrict__ V) {
+                                  int n, const int* __restrict__ qubits, int g, C2* __restrict__ V) {
   const int b = blockIdx.x;
-  const int x = bits[(long long)b * n + qubit];
-  const C2* src = W + (long long)b * 2 * r + (long long)x * r;
+  int x = 0;   // the tensor's physical index: its g qubits, the first the most significant bit
+  for (int j = 0; j < g; ++j) x = (x << 1) | (bits[(long long)b * n + qubits[j]] & 1);
+  const C2* src = W + (long long)b * ((long long)r << g) + (long long)x * r;
   C2* dst = V + (long long)b * r;
   for (int c = threadIdx.x; c < r; c += blockDim.x) dst[c] = src[c];
 }
@@ -161,14 +162,14 @@ cudaError_t readout_start(void* V, int B, bool fp64, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, int qubit, void* V, bool fp64,
-                       cudaStream_t st) {
+cudaError_t amp_select(const void* W, int B, int r, const unsigned char* bits, int n, const int* qubits, int g,
+                       void* V, bool fp64, cudaStream_t st) {
   const int threads = r >= 256 ? 256 : (r >= 64 ? 64 : 32);
   if (fp64)
-    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const double2*>(W), r, bits, n, qubit,
+    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const double2*>(W), r, bits, n, qubits, g,
                                              reinterpret_cast<double2*>(V));
   else
-    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const float2*>(W), r, bits, n, qubit,
+    amp_select_kernel<<<B, threads, 0, st>>>(reinterpret_cast<const float2*>(W), r, bits, n, qubits, g,
                                              reinterpret_cast<float2*>(V));
   return cudaGetLastError();
 }

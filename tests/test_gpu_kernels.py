@@ -253,6 +253,32 @@ def test_gram_eigensolver_declines_unresolved_spectra():
     assert proj.min() > 1 - 1e-4
 
 
+def test_gram_eigensolver_tiny_last_off_diagonal():
+    """H = G G^+ block-diagonal, its last block 2 x 2 with an off-diagonal of
+    -1e-15 i: the reduction leaves that entry as the tridiagonal form's last
+    off-diagonal, and the phase reflector that makes it real would have
+    tau ~ 1/|x|^2, beyond FP32, which the back-transformation would spread
+    into every kept vector.  The reduction drops such a column instead (a
+    perturbation far below the Gram's rounding): the vectors stay finite,
+    orthonormal and optimal."""
+    from paper_2207_05612_gb300 import binding
+    rng = np.random.default_rng(8)
+    m, n = 256, 300
+    g = np.zeros((m, n), dtype=np.complex128)
+    g[:m - 2, :n - 2] = _rand(rng, (m - 2, n - 2)) / np.sqrt(2 * m)
+    g[m - 2, n - 2] = 1.0
+    g[m - 1, n - 2] = 1e-15j
+    g[m - 1, n - 1] = 1.0
+    want = np.linalg.svd(g, compute_uv=False)
+    s, k, uk = binding.dmrgc_test_svd_gram(2, g, 128, 2e-5)
+    assert k == 128
+    assert np.all(np.isfinite(uk))
+    assert np.abs(s[:k + 1] - want[:k + 1]).max() <= 3e-5 * want[0]
+    assert np.abs(uk.conj().T @ uk - np.eye(k)).max() < 1e-4
+    f_opt = float(np.sum(want[:k] ** 2))
+    assert abs(_weight(g, uk) - f_opt) <= 1e-5 * f_opt
+
+
 def test_gram_eigensolver_degenerate_spectrum():
     """Exactly degenerate singular values (multiplets of 4) above the cut:
     inverse iteration inside a cluster is orthogonalised, so the kept vectors

@@ -343,6 +343,31 @@ def test_gram_eigensolver_path_in_the_sweep(prec):
         c.close()
 
 
+def test_gram_eigensolver_deeply_truncated_36_qubits():
+    """A 36-qubit run (6 x 6, chi = 128, five two-cycle steps, BF16x3, the
+    compressed MPO) deep in the truncated regime (f_delta ~ 0.03 per step).
+    It stopped with a non-finite weight until the tridiagonalisation dropped
+    columns below 1e-12 and the back-transformation flagged non-finite
+    vectors.  It completes with the eigensolver doing most SVDs, every partial
+    fidelity is finite and in (0, 1], and within each layer f never decreases
+    (Sec. IV.B.1) beyond rounding.  (log F~ itself is not compared with the
+    Jacobi-only run: two sweeps from a zip-up guess of f ~ 2e-4 stop far from
+    convergence, and runs in different arithmetic end up to 30% apart per
+    step.)"""
+    b = sc.batch_instances(256, seed=0)[167]
+    assert (b.rows, b.cols, b.chi) == (6, 6, 128)
+    ctx, per = gpu_run(b.circuit, b.chi, precision=1, svd_path=0, mpo_compress=1)
+    st = ctx.stats()
+    print(f"log F~ {ctx.fidelity()[0]:.6f}; eigensolver SVDs {st['eig_svds']}, fallbacks {st['eig_fallbacks']}")
+    assert st["eig_svds"] > 100
+    assert np.isfinite(ctx.fidelity()[0])
+    for p in per:
+        h = np.array(p["hist"])
+        assert np.all((h > 0) & (h <= 1 + 1e-4))
+        assert np.all(np.diff(h) >= -1e-3 * h[1:])
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_tensor_core_modes_are_reproducible(prec):
     """Split-K partials are summed in a fixed order: two runs of one circuit

@@ -9,6 +9,7 @@ not depend on the gauge of the bonds, so no phase is free)."""
 import numpy as np
 import pytest
 
+from oracle import dmrg as od
 from oracle import mpo as om
 from oracle import single_site as ss
 from oracle import statevector as sv
@@ -138,6 +139,25 @@ def test_grouped_context_rejects_what_it_does_not_do():
     ctx.apply_layer(circ.layers[0])
     ctx.sweep(1)
     with pytest.raises(binding.DmrgcError):
-        ctx.amplitude(np.zeros((1, 12), dtype=np.uint8))
-    with pytest.raises(binding.DmrgcError):
         ctx.sample(4, 1)
+
+
+@pytest.mark.parametrize("kind,widths,chi", [("V", [1, 2, 1], 4), ("D", [2, 2, 2], 6)])
+def test_grouped_amplitudes_and_metropolis_fp64(kind, widths, chi):
+    """Amplitudes of the grouped GPU state equal the oracle's state's (the
+    state is unique, no phase is free), and Metropolis chains on it equal the
+    oracle's chains on the oracle's amplitudes."""
+    rows, cols = 3, 4
+    circ = sc.random_circuit(rows, cols, 6, seed=21)
+    sizes = sc.grouping(rows, cols, kind, widths)
+    order, want = _oracle(circ, rows, cols, kind, sizes, chi, 3)
+    ctx, _ = _gpu(circ, rows, cols, kind, sizes, chi, 3)
+    dense = ss.group_dense(want[-1][1], sizes, order)
+    bits = sc.random_bitstrings(rows * cols, 300, seed=2)
+    got = ctx.amplitude(bits)
+    exp = sv.amplitudes(dense, bits)
+    assert np.abs(got - exp).max() < 1e-10
+    amp = lambda b: sv.amplitudes(dense, b)
+    w_s, w_acc = od.metropolis(amp, rows * cols, 16, 20, 3)
+    g_s, g_acc = ctx.metropolis(16, 20, 3)
+    assert g_acc == w_acc and np.array_equal(g_s, w_s)

@@ -81,3 +81,21 @@ def test_batch_item_layout_and_host_validation():
     opt.precision = 0
     opt.svd_mode = 2   # the learned mode without a rank model
     assert lib.dmrgc_batch_run(items, 1, 1, ctypes.byref(opt), None, ctypes.byref(wall)) == binding.DMRGC_EINVAL
+
+
+def test_grouped_create_validates_on_the_host():
+    """dmrgc_create_grouped rejects group sizes that do not tile the qubits, or
+    a grid order it does not know, before any CUDA call."""
+    import numpy as np
+    from paper_2207_05612_gb300 import binding
+    lib = binding.lib()
+    opt = binding.dmrgc_default_options()
+    h = ctypes.c_void_p()
+    for rows, cols, order, sizes in ((3, 4, 0, [3, 3, 3]), (3, 4, 0, [12, 0]), (3, 4, 0, [21, -9]),
+                                     (3, 4, 3, [6, 6]), (3, 4, 0, [])):
+        gs = np.ascontiguousarray(sizes or [1], dtype=np.int32)
+        g = binding.Grid(rows, cols, order)
+        st = lib.dmrgc_create_grouped(rows * cols, ctypes.byref(g), gs.ctypes.data, len(sizes), 8,
+                                      ctypes.byref(opt), ctypes.byref(h))
+        assert st == binding.DMRGC_EINVAL, (order, sizes)
+        assert not h.value
