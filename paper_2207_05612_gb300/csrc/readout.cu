@@ -23,18 +23,6 @@ __device__ __forceinline__ double splitmix64_uniform(unsigned long long seed, un
   return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double t = 0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) t += red[i];
-  return t;
-}
-
 // Batched read-outs.  Per site i the running row vectors of a chunk of B
 // strings, V[B][l], are multiplied by the whole site tensor as one GEMM
 // (W[b][x r + c] = sum_a V[b][a] A_i[a][x][c], done by the contraction engine
@@ -56,7 +44,11 @@ __global__ void amp_select_kernel(const C2* __restrict__ W, int r, const unsigne
 // sampling: p_x = |W_x|^2 (site at or right of the centre, T = null) or
 // Re sum_c T[b][x r + c] conj(W[b][x r + c]) with T = W E_i (left of it);
 // bit 0 iff u < p_0 / (p_0 + p_1), u = SplitMix64 at counter j N + i for
-// global sample j = row0 + b; V'[b] = W_x[b] / sqrt(p_x).
+// global sample j = row0 + b; V'[b] = W_x[b] / sqrt(p_x).  The terms and the
+// warp sums are in the storage precision, the sum of the warp sums in FP64
+// by thread 0 alone: FP64 arithmetic in every thread would bound the
+// complex64 kernel by GB300's FP64 rate (1/64 of FP32) instead of by HBM.
+// (In the FP64 mode this is the plain FP64 sum in the same order.)
 template <typename C2>
 __global__ void sample_select_kernel(const C2* __restrict__ W, const C2* __restrict__ T, int r,
                                      unsigned long long seed, long long row0, int n, int site, int qubit,
@@ -67,21 +59,35 @@ __global__ void sample_select_kernel(const C2* __restrict__ W, const C2* __restr
   const int b = blockIdx.x;
   const C2* w = W + (long long)b * 2 * r;
   const C2* t = T ? T + (long long)b * 2 * r : nullptr;
-  double p0 = 0, p1 = 0;
+  using R = decltype(w->x);
+  R q0 = 0, q1 = 0;
   for (int c = threadIdx.x; c < r; c += blockDim.x) {
     const C2 a0 = w[c], a1 = w[r + c];
     if (t) {
       const C2 e0 = t[c], e1 = t[r + c];
-      p0 += (double)e0.x * a0.x + (double)e0.y * a0.y;
-      p1 += (double)e1.x * a1.x + (double)e1.y * a1.y;
+      q0 += e0.x * a0.x + e0.y * a0.y;
+      q1 += e1.x * a1.x + e1.y * a1.y;
     } else {
-      p0 += (double)a0.x * a0.x + (double)a0.y * a0.y;
-      p1 += (double)a1.x * a1.x + (double)a1.y * a1.y;
+      q0 += a0.x * a0.x + a0.y * a0.y;
+      q1 += a1.x * a1.x + a1.y * a1.y;
     }
   }
-  p0 = block_sum(p0, red);
-  p1 = block_sum(p1, red);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+    q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = (double)q0;
+    red[16 + (threadIdx.x >> 5)] = (double)q1;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double p0 = 0, p1 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      p0 += red[i];
+      p1 += red[16 + i];
+    }
     const long long j = row0 + b;
     const double u = splitmix64_uniform(seed, (unsigned long long)j * n + site);
     const double tot = p0 + p1;

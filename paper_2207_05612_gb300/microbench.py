@@ -5,6 +5,7 @@ single kernel.
   python -m paper_2207_05612_gb300.microbench gemm --precision bf16x3 --m 65536 --n 1024 --k 512
   python -m paper_2207_05612_gb300.microbench svd --precision fp32 --m 1024 --n 1024 [--jacobi gram]
   python -m paper_2207_05612_gb300.microbench gram --precision tf32x3 --m 1024 --n 1024
+  python -m paper_2207_05612_gb300.microbench readout --precision bf16x3 --rows 6 --cols 9 --chi 512 --count 16384
 
 gemm: C = A B through dmrgc_test_gemm (host complex128 buffers in and out, so
 the wall time includes the transfers and the operand split); reports the wall
@@ -18,6 +19,12 @@ dmrgc_test_svd_gram (host buffers in and out): the Gram product, the
 tridiagonalisation, bisection, inverse iteration, the cluster pass and the
 back-transformation, one launch each per call; reports the wall time per call
 and the largest error of the kept singular values against LAPACK.
+readout: a seeded random right-canonical MPS (rows x cols qubits, bonds
+min(2^i, 2^(N-i), chi)) loaded with dmrgc_set_mps, then one amplitude call
+for `count` random bit strings and one sampling call for `count` samples
+(one per site: a chunk GEMM V A and the select kernel); reports the wall time
+of each call and the algorithmic bytes of one select launch at the largest
+bond.
 """
 from __future__ import annotations
 
@@ -104,15 +111,62 @@ def bench_gram(prec: int, m: int, n: int, reps: int, seed: int) -> dict:
             "max_rel_err_kept_s": err, "note": "wall time includes host<->device copies"}
 
 
+def random_right_canonical(n: int, chi: int, rng) -> list:
+    """Tensors [chi_l][2][chi_r] whose sites 1..n-1 have orthonormal rows of
+    the (chi_l, 2 chi_r) reshape and site 0 unit norm: a normalised state."""
+    bonds = [min(2 ** i, 2 ** (n - i), chi) for i in range(n + 1)]
+    mps = [None] * n
+    for i in range(n - 1, 0, -1):
+        cl, cr = bonds[i], bonds[i + 1]
+        q, _ = np.linalg.qr(_cplx(rng, (cl, 2 * cr)).conj().T)
+        mps[i] = q.conj().T.reshape(cl, 2, cr)
+    a0 = _cplx(rng, (1, 2, bonds[1]))
+    mps[0] = a0 / np.linalg.norm(a0)
+    return mps
+
+
+def bench_readout(prec: int, rows: int, cols: int, chi: int, count: int, seed: int) -> dict:
+    rng = np.random.default_rng(seed)
+    n = rows * cols
+    mps = random_right_canonical(n, chi, rng)
+    ctx = binding.Context(rows, cols, chi, precision=prec)
+    ctx.set_mps(mps)
+    bits = rng.integers(0, 2, size=(count, n), dtype=np.uint8)
+    ctx.amplitude(bits[:16])   # warm-up: one launch per site
+    t0 = time.perf_counter()
+    amp = ctx.amplitude(bits)
+    t_amp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    smp = ctx.sample(count, seed)
+    t_smp = time.perf_counter() - t0
+    ctx.close()
+    esz = 16 if prec == binding.DMRGC_FP64 else 8
+    bonds = [a.shape[2] for a in mps]
+    # per site, W [count][2 chi_r] is the chain GEMM's output: the amplitude
+    # select reads the chosen half and writes V [count][chi_r]; the sampling
+    # select reads both halves (p_0, p_1) and writes V
+    mb = max(bonds)
+    return {"kernel": "readout", "n_qubits": n, "chi": chi, "count": count,
+            "amplitude_wall_ms": t_amp * 1e3, "sample_wall_ms": t_smp * 1e3, "max_bond": mb,
+            "amp_select_bytes_at_max_bond": count * 2 * mb * esz,
+            "sample_select_bytes_at_max_bond": count * 3 * mb * esz,
+            "amp_finite": bool(np.all(np.isfinite(amp))), "samples_shape": list(smp.shape),
+            "note": "wall times include host<->device copies of bits, amplitudes and samples"}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["gemm", "svd", "gram"])
+    ap.add_argument("kernel", choices=["gemm", "svd", "gram", "readout"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--m", type=int, default=1024)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--k", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=6, help="readout: grid rows")
+    ap.add_argument("--cols", type=int, default=9, help="readout: grid columns")
+    ap.add_argument("--chi", type=int, default=512, help="readout: bond dimension")
+    ap.add_argument("--count", type=int, default=16384, help="readout: bit strings and samples")
     ap.add_argument("--jacobi", default="wp4", choices=["wp4", "gram"],
                     help="complex64 Jacobi kernel for m <= 1024")
     a = ap.parse_args(argv)
@@ -122,6 +176,8 @@ def main(argv=None) -> int:
         out = bench_gemm(prec, a.m, a.n, a.k, a.reps, a.seed)
     elif a.kernel == "gram":
         out = bench_gram(prec, a.m, a.n, a.reps, a.seed)
+    elif a.kernel == "readout":
+        out = bench_readout(prec, a.rows, a.cols, a.chi, a.count, a.seed)
     else:
         out = bench_svd(prec, a.m, a.n, a.reps, a.seed)
     out["precision"] = a.precision
