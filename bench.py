@@ -184,18 +184,26 @@ def stratified_bonds(shapes, count: int):
     return [order[min(len(order) - 1, int((k + 0.5) * len(order) / count))] for k in range(count)]
 
 
-def _oracle_worker(shapes, budget_s, seed, max_updates, q):
-    q.put(oracle_updates(shapes, budget_s, seed, max_updates))
+def reference_step(shapes):
+    """One step of the reference arm: an oracle update at each of the four
+    stratum bonds (their mean time estimates the layer's mean update).
+    Returns (updates, seconds, threads, bonds)."""
+    return oracle_updates(shapes, float("inf"), seed=0, max_updates=4)
 
 
-def oracle_updates_bounded(shapes, budget_s: float, timeout_s: float, seed: int = 0, max_updates: int = 1 << 30):
+def _oracle_worker(shapes, budget_s, seed, max_updates, whole_rounds, q):
+    q.put(oracle_updates(shapes, budget_s, seed, max_updates, whole_rounds))
+
+
+def oracle_updates_bounded(shapes, budget_s: float, timeout_s: float, seed: int = 0, max_updates: int = 1 << 30,
+                           whole_rounds: bool = False):
     """oracle_updates in a spawned process that is stopped after timeout_s
     (one oracle update cannot be interrupted from inside).  Returns the
     result, or None on timeout."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_worker, args=(shapes, budget_s, seed, max_updates, q))
+    p = ctx.Process(target=_oracle_worker, args=(shapes, budget_s, seed, max_updates, whole_rounds, q))
     p.start()
     try:
         return q.get(timeout=timeout_s)
@@ -208,12 +216,14 @@ def oracle_updates_bounded(shapes, budget_s: float, timeout_s: float, seed: int 
             p.join(5)
 
 
-def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 << 30):
+def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 << 30,
+                   whole_rounds: bool = False):
     """Oracle two-site updates (Sec. IV.B: X, Y, theta, truncated SVD, left
     environment) on random tensors of the given shapes (the cost does not
     depend on the values), at four bonds spread over the layer's cost order
-    taken in turn, until budget_s of CPU time or max_updates.  Returns
-    (updates, seconds, threads, bonds)."""
+    taken in turn, until budget_s of CPU time or max_updates; whole_rounds
+    also finishes the round of four bonds it is in, so that every stratum
+    counts equally.  Returns (updates, seconds, threads, bonds)."""
     from oracle import dmrg as od
     rng = np.random.default_rng(seed)
 
@@ -222,7 +232,7 @@ def oracle_updates(shapes, budget_s: float, seed: int = 0, max_updates: int = 1 
 
     done, spent, picked = 0, 0.0, []
     strata = stratified_bonds(shapes, 4)
-    while done < max_updates and (done == 0 or spent < budget_s):
+    while done < max_updates and (done == 0 or spent < budget_s or (whole_rounds and done % len(strata))):
         i = strata[(done + seed) % len(strata)]
         cl, dl, cm, dm, cr, dr = shapes[i]
         lenv, renv = rnd(cl, dl, cl), rnd(cr, dr, cr)
@@ -480,17 +490,18 @@ def main(argv=None):
         circ = sc.random_circuit(args.rows, args.cols, max(20, 2 * (args.warmup + args.steps)), seed=args.seed)
         shapes = workload_shapes(args.rows, args.cols, args.chi, circ.layers[args.warmup],
                                  compress=bool(args.mpo_compress))
-        times = []
-        threads = 1
-        for k in range(args.warmup + args.steps):
-            done, dt, threads, _ = oracle_updates(shapes, 0.0, seed=k, max_updates=1)
-            if k >= args.warmup:
-                times.append(dt)
-        tot = sum(times)
-        value = args.steps / tot
-        sample = (f"per step one oracle two-site update, the bonds taken in turn from four cost strata of the "
-                  f"first timed layer's bonds (the workload's operand shapes: saturated MPS bonds <= {args.chi}, "
-                  f"the layer's compressed MPO bonds; random values)")
+        for _ in range(args.warmup):   # untimed: one update at the cheapest stratum warms the BLAS threads
+            oracle_updates(shapes, 0.0, seed=0, max_updates=1)
+        tot, ups, threads = 0.0, 0, 1
+        for _ in range(args.steps):
+            done, dt, threads, _ = reference_step(shapes)
+            tot += dt
+            ups += done
+        value = ups / tot
+        sample = (f"per step four oracle two-site updates, one at the middle bond of each of four equal-frequency "
+                  f"cost strata of the first timed layer's bonds, so that their mean is the layer's mean update "
+                  f"(the workload's operand shapes: saturated MPS bonds <= {args.chi}, the layer's compressed MPO "
+                  f"bonds; random values)")
         line = {"impl": "reference", "metric": "two-site updates/s", "value": value,
                 "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -546,7 +557,7 @@ def main(argv=None):
     if not args.no_cpu_baseline and world == 1:
         note("CPU baseline")
         shapes = workload_shapes(args.rows, args.cols, args.chi, r["first_layer"], compress=bool(args.mpo_compress))
-        got = oracle_updates_bounded(shapes, args.cpu_budget, 6 * args.cpu_budget + 120, seed=1)
+        got = oracle_updates_bounded(shapes, args.cpu_budget, 6 * args.cpu_budget + 120, seed=0, whole_rounds=True)
         if got is None:
             cpu = {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"no oracle update finished within {6 * args.cpu_budget + 120:.0f} s"}
@@ -555,8 +566,9 @@ def main(argv=None):
             done, spent, threads, picked = got
             note(f"CPU baseline: {done} updates in {spent:.1f} s")
             cpu = {"value": done / spent, "unit": "updates/s", "cores": threads, "kind": "oracle",
-                   "sample": f"{done} oracle two-site updates at bonds taken in turn from four cost strata "
-                             f"of the timed layer's {len(shapes)} bonds (operand shapes of the workload: saturated "
+                   "sample": f"{done} oracle two-site updates, whole rounds over the middle bonds of four "
+                             f"equal-frequency cost strata of the timed layer's {len(shapes)} bonds, so that their "
+                             f"mean is the layer's mean update (operand shapes of the workload: saturated "
                              f"MPS bonds <= {args.chi}, the layer's compressed MPO bonds; random values), "
                              f"{spent:.1f} s of CPU time, bonds {picked}"}
     line = {

@@ -88,3 +88,23 @@ def test_sequence_two_pattern_order():
         assert len(qs) == len(set(qs))
         count.update(tuple(sorted(p)) for p in pairs)
     assert set(count.values()) == {2} and len(count) == len(sc.all_edges(4, 5))
+
+
+def test_reference_step_visits_every_cost_stratum():
+    """A step of the reference arm times one oracle update at the middle bond
+    of each of four equal-frequency cost strata, so the mean of its updates
+    estimates the layer's mean update (a 3 x 4 grid at chi = 8 keeps it fast)."""
+    import bench
+    from synthetic import circuits as sc
+    circ = sc.random_circuit(3, 4, 4, seed=0)
+    shapes = bench.workload_shapes(3, 4, 8, circ.layers[1])
+    strata = bench.stratified_bonds(shapes, 4)
+    flops = sorted(bench.update_flops(s) for s in shapes)
+    assert [bench.update_flops(shapes[i]) for i in strata] == sorted(bench.update_flops(shapes[i]) for i in strata)
+    assert len(set(strata)) == 4
+    done, secs, threads, bonds = bench.reference_step(shapes)
+    assert done == 4 and secs > 0 and threads >= 1
+    assert sorted(bonds) == sorted(strata)
+    # the middle of each quarter of the cost order
+    for k, i in enumerate(strata):
+        assert bench.update_flops(shapes[i]) == flops[min(len(flops) - 1, int((k + 0.5) * len(flops) / 4))]
