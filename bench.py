@@ -546,7 +546,10 @@ def main(argv=None):
                 "peak_note": "CUDA-core FMA peak: 152 SMs x 128 FP32 lanes x 2 x sampled SM clock"
                              if not fp64 else "nominal FP64 1.25 TFLOP/s x sampled/max SM clock",
                 "work_note": "algorithmic flops: 16/3 n^3 + 8 n^2 k per Gram eigensolver SVD, "
-                             "Jacobi 16 m per pair visited + 14 m per rotation"}
+                             "Jacobi 16 m per pair visited + 14 m per rotation",
+                "traffic_note": "null: the class is several kernels per SVD; ncu of its largest, he_tridiag_kernel "
+                                "at n = 1024, read 8.4 MB (the 8 MB Gram once) and wrote 31 KB "
+                                "(profiles/eig_gram_1024x1024_tf32x3.md): latency-bound, not DRAM-bound"}
     if args.precision == "bf16x3":
         t = NCU_TRAFFIC["tc_gemm_bf16x3"]
         roof_gemm["traffic"] = t["bytes"]
