@@ -253,7 +253,9 @@ dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count
  * u |<x|Psi>|^2 < |<x'|Psi>|^2.  Amplitudes as dmrgc_amplitude, all chains
  * of a step in one batch.  out_bits: host uint8 [chains][steps][n_qubits],
  * the string of each chain after each step (qubit order); *accepted (may be
- * NULL): moves made at steps >= 1.  Contexts with one qubit per tensor. */
+ * NULL): moves made at steps >= 1.  Any context, grouped ones included
+ * (the amplitudes read the grouped tensors directly).  EINVAL when chains or
+ * steps < 1, out_bits is NULL or chains x (steps + 1) exceeds 2^40. */
 dmrgc_status dmrgc_metropolis(dmrgc_ctx* ctx, int chains, int steps, unsigned long long seed,
                               unsigned char* out_bits, long long* accepted);
 
