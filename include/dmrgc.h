@@ -106,8 +106,10 @@ typedef struct {
                                  G G^+ (TF32x3 product, Householder tridiagonalisation,
                                  bisection and FP64 inverse iteration, back-transformation)
                                  whenever every kept eigenvalue is at least 1e-5 of the largest
-                                 (the Gram's rounding then cannot move the kept subspace), the
-                                 Jacobi SVD otherwise; 1 = always the Jacobi SVD.  FP64 mode
+                                 (the Gram's rounding then cannot move the kept subspace) and a
+                                 count set by the cutoff has cutoff^2 at or above that level,
+                                 the Jacobi SVD otherwise or when the eigensolver meets a
+                                 non-finite value; 1 = always the Jacobi SVD.  FP64 mode
                                  always uses the Jacobi SVD. */
 } dmrgc_options;
 
@@ -137,7 +139,8 @@ typedef struct {
   long long rsvd_attempts;      /* randomized SVDs tried (svd_mode 1, 2) */
   long long rsvd_accepted;      /* of which accepted (the rest fell back to Jacobi) */
   long long eig_svds;           /* truncated SVDs done by the Gram eigensolver (svd_path 0) */
-  long long eig_fallbacks;      /* Gram eigensolver results not resolved: redone by Jacobi */
+  long long eig_fallbacks;      /* Gram eigensolver results not resolved or not finite: redone by
+                                   Jacobi */
   long long eig_skipped;        /* SVDs sent straight to Jacobi: the last one at that bond was not
                                    resolvable by the eigensolver */
 } dmrgc_stats;
