@@ -16,7 +16,8 @@
 //     every CTA then forms w = p - (1/2) Re(conj(tau) u^+ p) u itself.
 //     complex64 arithmetic.  The reflectors follow the LAPACK zlarfg
 //     convention (complex tau, real beta), so T is real: the last one, of
-//     size 1, only makes the final off-diagonal real.
+//     size 1, only makes the final off-diagonal real.  A column below 1e-12
+//     gets none (its tau would overflow FP32).
 //  2. tri_bisect_kernel, tri_invit_kernel, tri_cluster_kernel: the leading
 //     eigenvalues of T by Sturm-count multisection (FP32, one warp per
 //     eigenvalue); their eigenvectors by inverse iteration in FP64 (the small
