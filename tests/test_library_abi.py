@@ -99,3 +99,21 @@ def test_grouped_create_validates_on_the_host():
                                       ctypes.byref(opt), ctypes.byref(h))
         assert st == binding.DMRGC_EINVAL, (order, sizes)
         assert not h.value
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_is_plain_c(lang, std):
+    """include/dmrgc.h compiles on its own as strict C99 and as C++ (plain
+    types and pointers only, nothing from CUDA or torch); the source is fed on
+    stdin, so nothing is written."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = ('#include "dmrgc.h"\n'
+           "int main(void) { dmrgc_options o; dmrgc_status s = dmrgc_default_options(&o);"
+           " return (int)s + o.precision; }\n")
+    r = subprocess.run([cc, "-x", lang, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), "-"], input=src, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
