@@ -454,7 +454,13 @@ dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, 
 dmrgc_status dmrgc_svd_noalloc(int precision, int m, int n, void* G, int chi, double rel_cut,
                                double* s_out, int* k_out, void* U_out, void* stream);
 
+/* Message of the context's most recent failure (empty if no call has failed
+ * yet; a later success does not clear it); the string is owned by the context
+ * and valid until its next call.  A NULL context gives "null context". */
 const char* dmrgc_last_error(const dmrgc_ctx* ctx);
+
+/* Synchronise the context's stream and free every device and host buffer it
+ * owns; ctx may be NULL.  The context must not be used afterwards. */
 void dmrgc_destroy(dmrgc_ctx* ctx);
 
 #ifdef __cplusplus
