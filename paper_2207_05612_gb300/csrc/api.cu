@@ -1360,6 +1360,7 @@ dmrgc_status dmrgc_batch_run(dmrgc_batch_item* items, int count, int n_workers, 
 }
 
 dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gates) {
+  Range nvtx_range("dmrgc_apply_layer");
   if (!c) return DMRGC_EINVAL;
   if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(c, DMRGC_EINVAL, "bad gate list");
   if (c->phase == 1) {   // commit the previous step: its state becomes |Psi_Q(D)>
@@ -1387,6 +1388,7 @@ dmrgc_status dmrgc_apply_layer(dmrgc_ctx* c, const dmrgc_gate* gates, int n_gate
 }
 
 dmrgc_status dmrgc_sweep(dmrgc_ctx* c, int n_sweeps, double* f_last) {
+  Range nvtx_range("dmrgc_sweep");
   if (!c) return DMRGC_EINVAL;
   if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep before dmrgc_apply_layer");
   if (n_sweeps < 0) return fail(c, DMRGC_EINVAL, "n_sweeps < 0");
@@ -1483,6 +1485,7 @@ dmrgc_status amplitudes_device(dmrgc_ctx* c, const unsigned char* bits_dev, long
 extern "C" {
 
 dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long count, double* out_re_im) {
+  Range nvtx_range("dmrgc_amplitude");
   if (!c) return DMRGC_EINVAL;
   if (count < 0 || (count > 0 && (!bits || !out_re_im))) return fail(c, DMRGC_EINVAL, "bad amplitude arguments");
   if (count == 0) return DMRGC_OK;
@@ -1500,6 +1503,7 @@ dmrgc_status dmrgc_amplitude(dmrgc_ctx* c, const unsigned char* bits, long long 
 
 dmrgc_status dmrgc_metropolis(dmrgc_ctx* c, int chains, int steps, unsigned long long seed, unsigned char* out_bits,
                               long long* accepted) {
+  Range nvtx_range("dmrgc_metropolis");
   if (!c) return DMRGC_EINVAL;
   if (chains < 1 || steps < 1 || !out_bits || (long long)chains * (steps + 1) > (1ll << 40))
     return fail(c, DMRGC_EINVAL, "bad metropolis arguments");
@@ -1539,6 +1543,7 @@ dmrgc_status dmrgc_metropolis(dmrgc_ctx* c, int chains, int steps, unsigned long
 }
 
 dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
+  Range nvtx_range("dmrgc_overlap");
   if (!a || !b || !out_re_im) return DMRGC_EINVAL;
   dmrgc_ctx* c = a;   // errors are reported on a
   if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64 || a->order != b->order)
@@ -1587,6 +1592,7 @@ dmrgc_status dmrgc_overlap(dmrgc_ctx* a, dmrgc_ctx* b, double* out_re_im) {
 
 dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* gates, int n_gates,
                                  double* out_re_im) {
+  Range nvtx_range("dmrgc_overlap_layer");
   if (!a || !b || !out_re_im || n_gates < 0 || (n_gates > 0 && !gates)) return DMRGC_EINVAL;
   dmrgc_ctx* c = a;   // errors are reported on a
   if (a->N != b->N || a->rows != b->rows || a->cols != b->cols || a->fp64 != b->fp64 || a->order != b->order)
@@ -1655,6 +1661,7 @@ dmrgc_status dmrgc_overlap_layer(dmrgc_ctx* a, dmrgc_ctx* b, const dmrgc_gate* g
 }
 
 dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed, unsigned char* out_bits) {
+  Range nvtx_range("dmrgc_sample");
   if (!c) return DMRGC_EINVAL;
   if (c->ng > 0) return fail(c, DMRGC_EINVAL, "sample: contexts with one qubit per tensor only");
   if (count < 0 || (count > 0 && !out_bits)) return fail(c, DMRGC_EINVAL, "bad sample arguments");
@@ -1727,6 +1734,7 @@ dmrgc_status dmrgc_sample(dmrgc_ctx* c, long long count, unsigned long long seed
 
 dmrgc_status dmrgc_xeb(dmrgc_ctx* sampled, dmrgc_ctx* reference, long long count, unsigned long long seed,
                        double* f_b, double* stderr_out) {
+  Range nvtx_range("dmrgc_xeb");
   if (!sampled || !reference || !f_b || count < 2 || count > (1LL << 26)) return DMRGC_EINVAL;
   dmrgc_ctx* c = sampled;
   if (sampled->N != reference->N || sampled->rows != reference->rows || sampled->cols != reference->cols)
@@ -1829,6 +1837,7 @@ dmrgc_status dmrgc_set_mps(dmrgc_ctx* c, const double* in_re_im, const int* bond
 }
 
 dmrgc_status dmrgc_sweep_updates(dmrgc_ctx* c, long long n_updates, double* f_last) {
+  Range nvtx_range("dmrgc_sweep_updates");
   if (!c) return DMRGC_EINVAL;
   if (c->phase != 1) return fail(c, DMRGC_ESTATE, "dmrgc_sweep_updates before dmrgc_apply_layer");
   if (n_updates < 0) return fail(c, DMRGC_EINVAL, "n_updates < 0");

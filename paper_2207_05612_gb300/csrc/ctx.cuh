@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace dmrgc_host {
@@ -100,12 +102,23 @@ dmrgc_status svd_columns(dmrgc_ctx* c, int m, int n, double rel_cut, bool square
                          int chi_cap = -1);
 
 // timing span of one class of device work (CUDA events on the context's stream)
+// NVTX range for the span of a host call (named in profilers and ncu's
+// --nvtx filters; without an attached tool the push and pop do nothing)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 struct Span {
   dmrgc_ctx* c;
   int cls;
   double flops;
   cudaEvent_t a = nullptr;
   Span(dmrgc_ctx* c_, int cls_, double flops_ = 0) : c(c_), cls(cls_), flops(flops_) {
+    static const char* const kName[] = {"contraction", "truncated SVD", "layer MPO", "other"};
+    nvtxRangePushA(kName[cls & 3]);
     if (c->opt.timing) {
       a = take_event(c);
       cudaEventRecord(a, c->st);
@@ -117,7 +130,10 @@ struct Span {
       cudaEventRecord(b, c->st);
       c->pend.push_back({cls, a, b, flops});
     }
+    nvtxRangePop();
   }
+  Span(const Span&) = delete;
+  Span& operator=(const Span&) = delete;
 };
 
 // single_site.cu: the random guess of a layer in orthogonal form, and sweeps

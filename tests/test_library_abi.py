@@ -117,3 +117,21 @@ def test_header_is_plain_c(lang, std):
     r = subprocess.run([cc, "-x", lang, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), "-"], input=src, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_entry_points_reject_a_null_context():
+    """The public calls return DMRGC_EINVAL for a NULL context before any CUDA
+    call (their NVTX ranges open and close without a profiler attached)."""
+    from paper_2207_05612_gb300 import binding
+    lib = binding.lib()
+    einval = binding.DMRGC_EINVAL
+    assert lib.dmrgc_apply_layer(None, None, 0) == einval
+    assert lib.dmrgc_sweep(None, 1, None) == einval
+    assert lib.dmrgc_sweep_updates(None, 1, None) == einval
+    assert lib.dmrgc_amplitude(None, None, 0, None) == einval
+    assert lib.dmrgc_sample(None, 0, 0, None) == einval
+    assert lib.dmrgc_metropolis(None, 1, 1, 0, None, None) == einval
+    assert lib.dmrgc_overlap(None, None, None) == einval
+    assert lib.dmrgc_fidelity(None, None, None) == einval
+    assert lib.dmrgc_last_error(None) == b"null context"
+    lib.dmrgc_destroy(None)
