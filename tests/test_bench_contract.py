@@ -111,3 +111,31 @@ def test_bench_line_has_every_contract_key(monkeypatch, capsys):
     assert line["excluding_mpo_and_guess"]["value"] == pytest.approx(2 * 106 / 0.020)
     assert line["excluding_mpo_and_guess"]["apply_layer_ms_per_step"] == pytest.approx(10.0)
     assert line["gpu_launches"] > 0
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """--impl reference (the oracle on the host cores) on a small grid: the
+    same metric and config keys, impl = reference, its own cpu_baseline and an
+    e2e without host-device traffic; value = the four stratum updates of each
+    step over their time."""
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    argv = ["--impl", "reference", "--steps", "2", "--warmup", "1", "--rows", "3", "--cols", "4", "--chi", "8"]
+    assert bench.main(argv) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "two-site updates/s"
+    assert line["unit"] == "updates/s" and line["higher_is_better"] is True and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["value"] == pytest.approx(2 * 4 / (2e-3 * line["ms_per_step"]))
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) == 0
+    assert capsys.readouterr().out.strip() == ""
